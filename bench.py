@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark: D3Q19 LES throughput (MLUPS) and HBM-roofline fraction on one B300.
+
+Workload: the turbulent open-channel LES, 256 x 128 x 128 cells (periodic
+x/z, bounce-back bottom, free-slip top, Smagorinsky C_s = 0.1, bulk-velocity
+controller, seeded log-law + 5 % initial state), statistics accumulation on.
+One step = one fused kernel over the whole grid (stream, canopy/driving
+force, Smagorinsky collision, boundaries, plane statistics).  The populations
+are resident in HBM; each step moves 152 B per cell (FP32 storage) or 76 B
+(FP16/BF16 shifted storage), 637 MB / 319 MB per step, well above the 126 MB L2,
+so no explicit L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+path does not exchange data between independent domains); rank 0 prints one
+JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 LES MLUPS & HBM-roofline fraction, fp32 vs fp16-store at stated error"
+WORKLOAD = ("turbulent channel LES 256x128x128 (periodic x/z, bounce-back bottom, free-slip "
+            "top, Cs=0.1, bulk-velocity controller, plane statistics on)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f16s", "bf16s"], default="f32")
+    ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16 storage legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows
+                                   if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------- our arm ---
+
+def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
+    import torch
+
+    case = W.channel_les()
+    d = P.Domain(case, storage)
+    if with_stats:
+        d.stats_reset(True)
+    stream = d.stream
+    d.step(warmup)
+    d.sync()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t_begin.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        d.step(1)
+        b.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    d.sync()
+    total_ms = t_begin.elapsed_time(t_end)
+    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    return d, case, total_ms, per_launch_ms
+
+
+def e2e_run(P, d, steps):
+    """Per step, through the public API: enqueue the step, then read the step's
+    result (the time-averaged plane statistics) into a host buffer; the call
+    synchronises, so every step pays its device->host copy."""
+    import numpy as np
+
+    out = np.zeros((9, d.case.stats_xbins, d.case.ny))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        d.step(1)
+        d.stats()
+    dt = time.perf_counter() - t0
+    d2h = out.nbytes + 4  # statistics + the device health flag
+    return dt, d2h
+
+
+def cpu_baseline(case_factory, seconds):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded sample of
+    the same workload (whole time steps of the full grid)."""
+    import oracle
+
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    case = case_factory()
+    o = oracle.Oracle(case)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    n = max(1, min(50, int(seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": case.cells * n / dt / 1e6, "unit": "MLUPS", "cores": threads,
+            "kind": "oracle", "sample": f"{n} full time steps of the {case.nx}x{case.ny}x{case.nz}"
+            f" channel (FP64, OpenMP over z planes, {threads} threads)"}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2206_15454_b300 as P
+    import workloads as W
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    storage = P.STORAGE_NAMES[args.storage]
+    hbm, peak_kind = peaks()
+    clocks = Clocks(local)
+    clocks.start()
+    d, case, total_ms, launch_ms = time_storage(P, W, storage, args.steps, args.warmup, ws)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(ws, total_ms)
+    cells = case.cells
+    bpl = P.BYTES_PER_LUP[storage]
+    value = cells * args.steps * ws / (total_ms * 1e-3) / 1e6
+    achieved = bpl * cells / (launch_ms * 1e-3) / 1e9
+    res = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f16s": "f16-storage/f32-compute",
+                  "bf16s": "bf16-storage/f32-compute"}[args.storage],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": cells, "storage": args.storage,
+                   "bytes_per_lup": bpl, "l2": "inputs larger than L2 (no flush needed)",
+                   "parallelism": f"{ws} independent replica(s)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": "step_kernel", "peak_kind": peak_kind,
+                     "launch_ms": launch_ms},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    # end to end through the public API with host-side results every step
+    e2e_steps = min(args.steps, 500)
+    dt, d2h = e2e_run(P, d, e2e_steps)
+    res["e2e"] = {"value": round(cells * e2e_steps * ws / dt / 1e6, 1), "unit": "MLUPS",
+                  "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+                  "note": "lbm_step + lbm_stats (host copy of plane statistics) per step; the "
+                          "flow state stays resident, so a step has no host input"}
+    d.close()
+    # half-precision storage legs (stated error against the FP32 run on the GPU)
+    if not args.no_half:
+        import numpy as np
+
+        ref = P.Domain(W.channel_les(), P.LBM_F32)
+        ref.step(100)
+        fref = ref.get_f()
+        ref.close()
+        for name in ("f16s", "bf16s"):
+            st = P.STORAGE_NAMES[name]
+            dh, _, tot, lms = time_storage(P, W, st, args.steps, args.warmup, ws)
+            dh.close()
+            tot = max_over_ranks(ws, tot)
+            ach = P.BYTES_PER_LUP[st] * cells / (lms * 1e-3) / 1e9
+            chk = P.Domain(W.channel_les(), st)
+            chk.step(100)
+            err = float(np.linalg.norm(chk.get_f() - fref) / np.linalg.norm(fref))
+            chk.close()
+            res[name] = {"value": round(cells * args.steps * ws / (tot * 1e-3) / 1e6, 1),
+                         "unit": "MLUPS", "ms_per_step": tot / args.steps,
+                         "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                                      "unit": "GB/s", "frac": round(ach / hbm, 4)},
+                         "rel_l2_f_vs_f32_after_100_steps": err}
+    if rank == 0 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(W.channel_les, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm ---
+
+def run_reference(args):
+    """The FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # calibrate a z-slab of the channel so that warmup + steps stay within ~2 minutes
+    probe = oracle.Oracle(W.channel_les(256, 128, 8))
+    t0 = time.perf_counter()
+    probe.step(1)
+    per_cell = (time.perf_counter() - t0) / (256 * 128 * 8)
+    probe.close()
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nz = int(max(1, min(128, budget / (per_cell * 256 * 128))))
+    case = W.channel_les(256, 128, nz)
+    o = oracle.Oracle(case)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = case.cells * args.steps / dt / 1e6
+    sample = (f"{args.steps} time steps of a 256x128x{nz} z-slab of the channel workload "
+              f"(FP64 oracle, {threads} OpenMP threads)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": case.cells, "sample_nz": nz},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

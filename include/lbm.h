@@ -1,0 +1,180 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) D3Q19 LBM-LES library.
+ *
+ * One call advances a uniform-grid large-eddy simulation by whole time steps
+ * of the lattice Boltzmann method of arxiv 2206.15454 (Sec. 2):
+ *   stream (pull) -> density and momentum (Eqs. density, momentum)
+ *   -> canopy drag F = -C_D a(y) |u| u (Eq. forestForce, Algorithm 1) solved
+ *      together with the half-force velocity shift of Eq. momentum
+ *   -> equilibrium (Eq. local_eq), non-equilibrium flux (Eq. tensor)
+ *   -> Smagorinsky relaxation time (Eqs. nu_t, strain, tau_total)
+ *   -> BGK relaxation (Eqs. lbe, bgk) + Guo forcing (Eq. bodyforce) -> store.
+ * Everything runs in hand-written CUDA kernels on one GPU; there is no CPU
+ * fallback.
+ *
+ * Conventions
+ *   Lattice units (dx = dt = 1, c_s^2 = 1/3).  Direction order:
+ *     0:(0,0,0) 1:(+1,0,0) 2:(-1,0,0) 3:(0,+1,0) 4:(0,-1,0) 5:(0,0,+1)
+ *     6:(0,0,-1) 7:(+1,+1,0) 8:(-1,-1,0) 9:(+1,-1,0) 10:(-1,+1,0)
+ *     11:(+1,0,+1) 12:(-1,0,-1) 13:(+1,0,-1) 14:(-1,0,+1) 15:(0,+1,+1)
+ *     16:(0,-1,-1) 17:(0,+1,-1) 18:(0,-1,+1).
+ *   Host population arrays (lbm_get_f / lbm_set_f) are FP64, unshifted,
+ *   layout f[q][z][y][x] with x fastest, 19*nx*ny*nz values.  The state is
+ *   the post-collision population set of the last completed step.
+ *   On the device the populations are stored as offsets from the lattice
+ *   weights, f_i - w_i, in FP32, FP16 or BF16 (lbm_storage), structure of
+ *   arrays [q][y][z][x] with rows padded to a multiple of 64 elements; two
+ *   population sets are kept (pull scheme, double buffered).
+ *
+ * Errors
+ *   Every call returns an lbm_status and never aborts.  An error other than
+ *   LBM_ERR_ARG is sticky: the context refuses further work until
+ *   lbm_destroy.  lbm_last_error() gives a one-line description.  lbm_step
+ *   is asynchronous on the context's stream; device-side failures (a
+ *   non-finite density, LBM_ERR_NAN) are reported by the next synchronising
+ *   call (lbm_sync, lbm_stats, lbm_mass, lbm_get_f, lbm_get_macro,
+ *   lbm_drive, lbm_save).
+ *
+ * Ownership
+ *   Input arrays are copied during the call.  Output arrays are owned by the
+ *   caller.  Device memory is either a caller-provided workspace (device
+ *   pointer plus size, e.g. from PyTorch's allocator, see
+ *   lbm_workspace_bytes) that must outlive the context, or allocated by the
+ *   library with cudaMalloc when workspace is NULL.
+ */
+#ifndef LBM_B300_H
+#define LBM_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument; the context (if any) is unchanged */
+    LBM_ERR_OOM = 2,      /* device or host allocation failed / workspace too small */
+    LBM_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    LBM_ERR_NAN = 4,      /* a cell produced a non-finite density or velocity */
+    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+    LBM_ERR_STATE = 6,    /* the context holds an earlier sticky error */
+    LBM_ERR_IO = 7        /* checkpoint file could not be written/read/verified */
+} lbm_status;
+
+/* Boundary kinds.  Supported combinations: x periodic or INFLOW(x_lo) with
+ * OUTFLOW(x_hi); y periodic, or BOUNCEBACK at y_lo with BOUNCEBACK,
+ * FREESLIP or EQUILIBRIUM at y_hi; z periodic. */
+typedef enum lbm_bc {
+    LBM_BC_PERIODIC = 0,
+    LBM_BC_BOUNCEBACK = 1,  /* halfway bounce-back (no-slip wall half a cell out) */
+    LBM_BC_FREESLIP = 2,    /* specular reflection of the wall-normal component */
+    LBM_BC_EQUILIBRIUM = 3, /* incoming populations = f_eq(rho = 1, u_top) */
+    LBM_BC_INFLOW = 4,      /* incoming populations = f_eq(rho = 1, u_in(y)) */
+    LBM_BC_OUTFLOW = 5      /* incoming populations copied from the last column */
+} lbm_bc;
+
+typedef enum lbm_storage {
+    LBM_F32 = 0,        /* f_i - w_i in FP32: 152 bytes moved per lattice update */
+    LBM_F16_SHIFTED = 1,  /* f_i - w_i in FP16 (round to nearest even): 76 B/LUP */
+    LBM_BF16_SHIFTED = 2  /* f_i - w_i in BF16 (round to nearest even): 76 B/LUP */
+} lbm_storage;
+
+typedef struct lbm_grid {
+    int32_t nx, ny, nz;              /* cells; each >= 1, nx*ny*nz < 2^31 */
+    int32_t x_lo, x_hi, y_lo, y_hi, z_lo, z_hi;  /* lbm_bc values */
+} lbm_grid;
+
+typedef struct lbm_forcing {
+    double g[3];            /* driving acceleration; the force density is rho*g
+                               (Eq. Body_force gives it as rho u_tau^2 / H) */
+    double cd;              /* canopy drag coefficient C_D (Sec. 2.3: 0.15) */
+    int32_t x_canopy_begin; /* the canopy covers x in [begin, end) ... */
+    int32_t x_canopy_end;   /* ... and the heights where lad[y] > 0 */
+    double u_bulk_target;   /* > 0: g[0] is corrected every step by
+                               ctrl_gain * (u_bulk_target - U_b), U_b the mean
+                               streamwise velocity of the previous step */
+    double ctrl_gain;
+    double u_top[3];        /* velocity of an EQUILIBRIUM top boundary */
+    const double* u_in_profile; /* ny streamwise velocities, or NULL (= 0): the
+                                   inflow profile and the initial mean profile */
+} lbm_forcing;
+
+/* Bytes of device workspace lbm_create needs for this grid and storage;
+ * 0 on invalid arguments. */
+size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t storage, int32_t stats_xbins);
+
+/* Create a domain and initialise it on the device to f = f_eq(1, u0) with
+ * u0 = (u_in_profile[y], 0, 0) + init_perturb * (r0, r1, r2), r_a the
+ * (3c + a)-th output of SplitMix64 seeded with `seed` mapped to [-1, 1)
+ * (c = (z*ny + y)*nx + x).
+ *   tau0   molecular relaxation time, > 0.5 (nu_0 = (tau0 - 1/2)/3)
+ *   cs     Smagorinsky constant C_s >= 0 (C_smag = C_s^2, filter width 1)
+ *   lad    ny leaf-area densities a(y) per lattice length at cell-centre
+ *          heights, or NULL for no canopy
+ *   stats_xbins  number of equal x-bins the statistics are kept for (>= 1)
+ *   workspace, workspace_bytes  caller-owned device memory of at least
+ *          lbm_workspace_bytes(), or NULL/0 to let the library allocate.
+ * The context uses the legacy default stream until lbm_set_stream. */
+lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double* lad,
+                      const lbm_forcing* forcing, int32_t storage, int32_t stats_xbins,
+                      uint64_t seed, double init_perturb, void* workspace,
+                      size_t workspace_bytes, lbm_ctx** out);
+
+/* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for every later launch and copy. */
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Enqueue n >= 0 time steps (one fused kernel per step).  Asynchronous. */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
+
+/* Wait for the context's stream and report device-side errors. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Zero the statistics accumulators; enable != 0 makes every following step
+ * add its velocities to them (Sec. 4: averaged in time, then over x-z planes). */
+lbm_status lbm_stats_reset(lbm_ctx* ctx, int32_t enable);
+
+/* Averages since the last reset: out holds 9 blocks of stats_xbins*ny
+ * doubles, [quantity][xbin][y]: <u>, <v>, <w>, <u'u'>, <v'v'>, <w'w'>,
+ * <u'v'>, <u'w'>, <v'w'> (covariances pooled over time, x and z).
+ * n must be >= 9*stats_xbins*ny.  *samples = time steps accumulated. */
+lbm_status lbm_stats(lbm_ctx* ctx, double* out, size_t n, int64_t* samples);
+
+/* Global mass: sum over cells and directions of the stored populations, FP64. */
+lbm_status lbm_mass(lbm_ctx* ctx, double* out);
+
+/* Copy the populations out / in (FP64 host array, see Conventions; n must be
+ * 19*nx*ny*nz).  lbm_set_f rounds to the storage type. */
+lbm_status lbm_get_f(lbm_ctx* ctx, double* host_f, size_t n);
+lbm_status lbm_set_f(lbm_ctx* ctx, const double* host_f, size_t n);
+
+/* Density and force-corrected velocity that the next step computes:
+ * rho[z][y][x] (n = nx*ny*nz values) and u[3][z][y][x] (3n values). */
+lbm_status lbm_get_macro(lbm_ctx* ctx, double* rho, double* u, size_t n);
+
+/* Driving acceleration the next step uses and the bulk velocity of the last. */
+lbm_status lbm_drive(lbm_ctx* ctx, double g[3], double* u_bulk);
+
+/* Checkpoint: header (grid, parameters, storage, step, statistics) plus the
+ * raw device populations, with an FNV-1a checksum; lbm_load verifies it
+ * against a context created with the same grid and storage. */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Steps completed since creation (or loaded from a checkpoint). */
+int64_t lbm_steps_done(const lbm_ctx* ctx);
+
+/* Release every resource (waits for the stream).  NULL is accepted. */
+void lbm_destroy(lbm_ctx* ctx);
+
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

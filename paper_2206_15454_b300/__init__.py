@@ -1,0 +1,278 @@
+"""B300 (sm_103a) D3Q19 LBM-LES library for forest-canopy boundary layers.
+
+Thin ctypes binding of the C ABI in ``include/lbm.h`` (same function names,
+argument marshalling only).  Every step of the method runs in the CUDA
+kernels of ``csrc/``; PyTorch only supplies device memory (the workspace) and
+the stream.  There is no CPU fallback: if the shared library is missing the
+import of any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_b300.so")
+
+Q = 19
+LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NAN, LBM_ERR_TIMEOUT, \
+    LBM_ERR_STATE, LBM_ERR_IO = range(8)
+LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK, LBM_BC_FREESLIP, LBM_BC_EQUILIBRIUM, LBM_BC_INFLOW, \
+    LBM_BC_OUTFLOW = range(6)
+LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = range(3)
+STORAGE_NAMES = {"f32": LBM_F32, "f16s": LBM_F16_SHIFTED, "bf16s": LBM_BF16_SHIFTED}
+BYTES_PER_LUP = {LBM_F32: 152, LBM_F16_SHIFTED: 76, LBM_BF16_SHIFTED: 76}
+
+
+class LbmGrid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("x_lo", C.c_int32), ("x_hi", C.c_int32), ("y_lo", C.c_int32),
+                ("y_hi", C.c_int32), ("z_lo", C.c_int32), ("z_hi", C.c_int32)]
+
+
+class LbmForcing(C.Structure):
+    _fields_ = [("g", C.c_double * 3), ("cd", C.c_double),
+                ("x_canopy_begin", C.c_int32), ("x_canopy_end", C.c_int32),
+                ("u_bulk_target", C.c_double), ("ctrl_gain", C.c_double),
+                ("u_top", C.c_double * 3), ("u_in_profile", C.POINTER(C.c_double))]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load the in-tree CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LbmError(LBM_ERR_CUDA, f"CUDA library missing: {LIB_PATH} (run build())")
+        L = C.CDLL(LIB_PATH)
+        vp, st = C.c_void_p, C.c_int32
+        L.lbm_workspace_bytes.restype = C.c_size_t
+        L.lbm_workspace_bytes.argtypes = [C.POINTER(LbmGrid), C.c_int32, C.c_int32]
+        L.lbm_create.restype = st
+        L.lbm_create.argtypes = [C.POINTER(LbmGrid), C.c_double, C.c_double, _DP,
+                                 C.POINTER(LbmForcing), C.c_int32, C.c_int32, C.c_uint64,
+                                 C.c_double, vp, C.c_size_t, C.POINTER(vp)]
+        for name, args in [("lbm_set_stream", [vp, vp]), ("lbm_step", [vp, C.c_int32]),
+                           ("lbm_sync", [vp]), ("lbm_stats_reset", [vp, C.c_int32]),
+                           ("lbm_stats", [vp, _DP, C.c_size_t, C.POINTER(C.c_int64)]),
+                           ("lbm_mass", [vp, _DP]), ("lbm_get_f", [vp, _DP, C.c_size_t]),
+                           ("lbm_set_f", [vp, _DP, C.c_size_t]),
+                           ("lbm_get_macro", [vp, _DP, _DP, C.c_size_t]),
+                           ("lbm_drive", [vp, _DP, _DP]), ("lbm_save", [vp, C.c_char_p]),
+                           ("lbm_load", [vp, C.c_char_p])]:
+            fn = getattr(L, name)
+            fn.restype = st
+            fn.argtypes = args
+        L.lbm_steps_done.restype = C.c_int64
+        L.lbm_steps_done.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_last_error.restype = C.c_char_p
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_status_string.restype = C.c_char_p
+        L.lbm_status_string.argtypes = [C.c_int32]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def _check(status, ctx=None, what=""):
+    if status != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode() if ctx else ""
+        base = lib().lbm_status_string(status).decode()
+        raise LbmError(status, f"{what}: {base}{(' - ' + msg) if msg else ''}")
+
+
+# ---- the C entry points, one to one -------------------------------------------------
+
+def lbm_workspace_bytes(grid: LbmGrid, storage: int, stats_xbins: int) -> int:
+    return int(lib().lbm_workspace_bytes(C.byref(grid), storage, stats_xbins))
+
+
+def lbm_create(grid, tau0, cs, lad, forcing, storage, stats_xbins, seed, init_perturb,
+               workspace=0, workspace_bytes=0):
+    ctx = C.c_void_p()
+    lad_p = _dp(lad) if lad is not None else _DP()
+    s = lib().lbm_create(C.byref(grid), tau0, cs, lad_p, C.byref(forcing), storage,
+                         stats_xbins, seed, init_perturb, C.c_void_p(workspace or None),
+                         workspace_bytes, C.byref(ctx))
+    _check(s, None, "lbm_create")
+    return ctx
+
+
+def lbm_set_stream(ctx, stream_ptr):
+    _check(lib().lbm_set_stream(ctx, C.c_void_p(stream_ptr or None)), ctx, "lbm_set_stream")
+
+
+def lbm_step(ctx, n):
+    _check(lib().lbm_step(ctx, int(n)), ctx, "lbm_step")
+
+
+def lbm_sync(ctx):
+    _check(lib().lbm_sync(ctx), ctx, "lbm_sync")
+
+
+def lbm_stats_reset(ctx, enable=True):
+    _check(lib().lbm_stats_reset(ctx, int(bool(enable))), ctx, "lbm_stats_reset")
+
+
+def lbm_stats(ctx, out: np.ndarray):
+    n = C.c_int64()
+    _check(lib().lbm_stats(ctx, _dp(out), out.size, C.byref(n)), ctx, "lbm_stats")
+    return int(n.value)
+
+
+def lbm_mass(ctx):
+    out = np.zeros(1)
+    _check(lib().lbm_mass(ctx, _dp(out)), ctx, "lbm_mass")
+    return float(out[0])
+
+
+def lbm_get_f(ctx, out: np.ndarray):
+    _check(lib().lbm_get_f(ctx, _dp(out), out.size), ctx, "lbm_get_f")
+
+
+def lbm_set_f(ctx, f: np.ndarray):
+    _check(lib().lbm_set_f(ctx, _dp(f), f.size), ctx, "lbm_set_f")
+
+
+def lbm_get_macro(ctx, rho: np.ndarray, u: np.ndarray):
+    _check(lib().lbm_get_macro(ctx, _dp(rho), _dp(u), rho.size), ctx, "lbm_get_macro")
+
+
+def lbm_drive(ctx):
+    g, ub = np.zeros(3), np.zeros(1)
+    _check(lib().lbm_drive(ctx, _dp(g), _dp(ub)), ctx, "lbm_drive")
+    return g, float(ub[0])
+
+
+def lbm_save(ctx, path):
+    _check(lib().lbm_save(ctx, str(path).encode()), ctx, "lbm_save")
+
+
+def lbm_load(ctx, path):
+    _check(lib().lbm_load(ctx, str(path).encode()), ctx, "lbm_load")
+
+
+def lbm_steps_done(ctx):
+    return int(lib().lbm_steps_done(ctx))
+
+
+def lbm_destroy(ctx):
+    lib().lbm_destroy(ctx)
+
+
+# ---- convenience: one domain with a PyTorch-owned workspace and stream ---------------
+
+class Domain:
+    """A simulation domain.  ``case`` is any object with the attributes of
+    ``workloads.Case`` (nx, ny, nz, bc_x/bc_y/bc_z pairs, tau0, cs, g, cd,
+    canopy_x, u_bulk_target, ctrl_gain, u_top, stats_xbins, seed,
+    init_perturb, lad, u_profile)."""
+
+    def __init__(self, case, storage=LBM_F32, use_torch_workspace=True, stream=None):
+        import torch
+
+        if isinstance(storage, str):
+            storage = STORAGE_NAMES[storage]
+        self.case, self.storage = case, storage
+        self.shape = (case.nz, case.ny, case.nx)
+        self.cells = case.nx * case.ny * case.nz
+        g = LbmGrid(case.nx, case.ny, case.nz, *case.bc_x, *case.bc_y, *case.bc_z)
+        self._uprof = (None if case.u_profile is None
+                       else np.ascontiguousarray(case.u_profile, dtype=np.float64))
+        fo = LbmForcing()
+        fo.g[:] = [float(v) for v in case.g]
+        fo.cd = case.cd
+        fo.x_canopy_begin, fo.x_canopy_end = case.canopy_x
+        fo.u_bulk_target, fo.ctrl_gain = case.u_bulk_target, case.ctrl_gain
+        fo.u_top[:] = [float(v) for v in case.u_top]
+        fo.u_in_profile = _dp(self._uprof) if self._uprof is not None else _DP()
+        lad = None if case.lad is None else np.ascontiguousarray(case.lad, dtype=np.float64)
+        self.workspace = None
+        ws_ptr, ws_bytes = 0, 0
+        if use_torch_workspace:
+            ws_bytes = lbm_workspace_bytes(g, storage, case.stats_xbins)
+            if ws_bytes == 0:
+                raise LbmError(LBM_ERR_ARG, "lbm_workspace_bytes: invalid grid/storage/bins")
+            self.workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+            ws_ptr = self.workspace.data_ptr()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        self.ctx = lbm_create(g, case.tau0, case.cs, lad, fo, storage, case.stats_xbins,
+                              case.seed, case.init_perturb, ws_ptr, ws_bytes)
+        lbm_set_stream(self.ctx, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def sync(self):
+        lbm_sync(self.ctx)
+
+    def get_f(self):
+        f = np.zeros((Q,) + self.shape)
+        lbm_get_f(self.ctx, f)
+        return f
+
+    def set_f(self, f):
+        lbm_set_f(self.ctx, np.ascontiguousarray(f, dtype=np.float64))
+
+    def macro(self):
+        rho, u = np.zeros(self.shape), np.zeros((3,) + self.shape)
+        lbm_get_macro(self.ctx, rho, u)
+        return rho, u
+
+    def mass(self):
+        return lbm_mass(self.ctx)
+
+    def stats_reset(self, enable=True):
+        lbm_stats_reset(self.ctx, enable)
+
+    def stats(self):
+        out = np.zeros((9, self.case.stats_xbins, self.case.ny))
+        n = lbm_stats(self.ctx, out)
+        return out, n
+
+    def drive(self):
+        return lbm_drive(self.ctx)
+
+    def save(self, path):
+        lbm_save(self.ctx, path)
+
+    def load(self, path):
+        lbm_load(self.ctx, path)
+
+    def steps_done(self):
+        return lbm_steps_done(self.ctx)
+
+
+def build(force=False):
+    from . import build as _b
+    return _b.build(force=force)

@@ -1,0 +1,640 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// Owns the context (grid, parameters, device buffers carved from one
+// workspace), enqueues the kernels of lbm_device.cuh on the context's stream,
+// and converts populations between the device storage ([q][y][z][x], shifted
+// by the lattice weights, FP32/FP16/BF16) and the public FP64 layout
+// ([q][z][y][x], unshifted).  No lattice Boltzmann arithmetic runs on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMassBlocks = 1024;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
+
+int pitch_of(int nx) { return (nx + 63) / 64 * 64; }
+
+struct Layout {
+  size_t f_bytes, stats_off, state_off, ubpart_off, kdrag_off, feqin_off, uprof_off, mass_off,
+      total;
+};
+
+Layout layout_of(const lbm_grid& g, int storage, int nbins) {
+  Layout L;
+  const size_t plane = (size_t)g.ny * g.nz * pitch_of(g.nx);
+  L.f_bytes = align_up(plane * NQ * elem_bytes(storage), kAlign);
+  size_t off = 2 * L.f_bytes;
+  L.stats_off = off;  off += align_up(sizeof(double) * 9 * nbins * g.ny, kAlign);
+  L.state_off = off;  off += align_up(sizeof(DevState), kAlign);
+  L.ubpart_off = off; off += align_up(sizeof(double) * 2 * MAX_BLOCKS, kAlign);
+  L.kdrag_off = off;  off += align_up(sizeof(float) * g.ny, kAlign);
+  L.feqin_off = off;  off += align_up(sizeof(float) * NQ * g.ny, kAlign);
+  L.uprof_off = off;  off += align_up(sizeof(double) * g.ny, kAlign);
+  L.mass_off = off;   off += align_up(sizeof(double) * (kMassBlocks + 1), kAlign);
+  L.total = off;
+  return L;
+}
+
+bool grid_ok(const lbm_grid* g) {
+  if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1) return false;
+  const long long cells = (long long)pitch_of(g->nx) * g->ny * g->nz;
+  if (cells >= (1ll << 31)) return false;
+  const bool xper = g->x_lo == LBM_BC_PERIODIC && g->x_hi == LBM_BC_PERIODIC;
+  const bool xio = g->x_lo == LBM_BC_INFLOW && g->x_hi == LBM_BC_OUTFLOW;
+  const bool yper = g->y_lo == LBM_BC_PERIODIC && g->y_hi == LBM_BC_PERIODIC;
+  const bool ywall = g->y_lo == LBM_BC_BOUNCEBACK &&
+                     (g->y_hi == LBM_BC_BOUNCEBACK || g->y_hi == LBM_BC_FREESLIP ||
+                      g->y_hi == LBM_BC_EQUILIBRIUM);
+  const bool zper = g->z_lo == LBM_BC_PERIODIC && g->z_hi == LBM_BC_PERIODIC;
+  return (xper || xio) && (yper || ywall) && zper;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_grid grid;
+  int storage = 0, nbins = 1;
+  double tau0 = 0, cs = 0;
+  lbm_forcing forcing;
+  std::vector<double> lad, uprof;
+  uint64_t seed = 0;
+  double init_perturb = 0;
+  int pitch = 0;
+  long long plane = 0, cells = 0;
+  Layout L;
+  char* ws = nullptr;
+  bool owns_ws = false;
+  cudaStream_t stream = nullptr;
+  int cur = 0;                // population set holding the current state
+  int64_t steps = 0;
+  bool stats_on = false;
+  int64_t stats_samples = 0;
+  float* macro_buf = nullptr;
+  int sm_count = 0, blocks_per_sm = 0;
+  int last_grid = 0;          // blocks of the previous step launch (partials to sum)
+  dim3 block;
+  int nxc = 0, nzg = 0;
+  lbm_status status = LBM_OK;
+  std::string err;
+
+  void* fbuf(int k) const { return ws + (size_t)k * L.f_bytes; }
+  double* stats() const { return reinterpret_cast<double*>(ws + L.stats_off); }
+  DevState* state() const { return reinterpret_cast<DevState*>(ws + L.state_off); }
+  double* ub_part() const { return reinterpret_cast<double*>(ws + L.ubpart_off); }
+  float* kdrag() const { return reinterpret_cast<float*>(ws + L.kdrag_off); }
+  float* feq_in() const { return reinterpret_cast<float*>(ws + L.feqin_off); }
+  double* uprof_dev() const { return reinterpret_cast<double*>(ws + L.uprof_off); }
+  double* mass_buf() const { return reinterpret_cast<double*>(ws + L.mass_off); }
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+  if (c && c->status == LBM_OK) {
+    c->status = s;
+    c->err = msg;
+  }
+  return s;
+}
+
+lbm_status arg_error(lbm_ctx* c, const std::string& msg) {
+  if (c) c->err = msg;  // argument errors are not sticky
+  return LBM_ERR_ARG;
+}
+
+#define CK(ctx, call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((ctx), LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Shifted equilibrium f_eq(1, u) - w_i in FP64 (for the boundary tables).
+void feq_shift(const double u[3], double out[NQ]) {
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int i = 0; i < NQ; i++) {
+    const double cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+    out[i] = wgt_d(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+  }
+}
+
+StepParams make_params(const lbm_ctx* c) {
+  StepParams p;
+  std::memset(&p, 0, sizeof(p));
+  const lbm_grid& g = c->grid;
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.pitch = c->pitch; p.plane = c->plane;
+  for (int i = 0; i < NQ; i++) p.qoff[i] = (long long)i * c->plane;
+  p.x_io = g.x_lo == LBM_BC_INFLOW;
+  p.y_walls = g.y_lo == LBM_BC_BOUNCEBACK;
+  p.top = g.y_hi == LBM_BC_BOUNCEBACK ? 1 : g.y_hi == LBM_BC_FREESLIP ? 2 : 3;
+  p.tau0 = (float)c->tau0;
+  p.c18 = (float)(18.0 * std::sqrt(2.0) * c->cs * c->cs);
+  for (int a = 0; a < 3; a++) p.g[a] = (float)c->forcing.g[a];
+  p.ctrl = c->forcing.u_bulk_target > 0.0;
+  p.g0x = c->forcing.g[0];
+  p.gain = c->forcing.ctrl_gain;
+  p.u_target = c->forcing.u_bulk_target;
+  p.inv_cells = 1.0 / (double)c->cells;
+  const int64_t t = c->steps;
+  p.have_prev = t > 0;
+  p.ub_part = c->ub_part();
+  p.slot_read = (int)((t + 1) % 2);
+  p.slot_write = (int)(t % 2);
+  p.nprev = c->last_grid;
+  p.canopy_x0 = c->forcing.x_canopy_begin;
+  p.canopy_x1 = c->forcing.x_canopy_end;
+  p.kdrag = c->lad.empty() ? nullptr : c->kdrag();
+  p.feq_in = p.x_io ? c->feq_in() : nullptr;
+  double ft[NQ];
+  feq_shift(c->forcing.u_top, ft);
+  for (int i = 0; i < NQ; i++) p.feq_top[i] = (float)ft[i];
+  p.nxc = c->nxc;
+  p.nzg = c->nzg;
+  p.ntiles = (long long)c->nxc * c->nzg * g.ny;
+  p.stats = c->stats();
+  p.nbins = c->nbins;
+  p.state = c->state();
+  p.src = c->fbuf(c->cur);
+  p.dst = c->fbuf(1 - c->cur);
+  return p;
+}
+
+int step_grid(const lbm_ctx* c) {
+  const long long ntiles = (long long)c->nxc * c->nzg * c->grid.ny;
+  const long long want = (long long)c->sm_count * c->blocks_per_sm;
+  return (int)std::max<long long>(1, std::min<long long>({want, ntiles, (long long)MAX_BLOCKS}));
+}
+
+template <int S>
+void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
+  const int grid = step_grid(c);
+  if (stats)
+    step_kernel<S, true><<<grid, c->block, 0, c->stream>>>(p);
+  else
+    step_kernel<S, false><<<grid, c->block, 0, c->stream>>>(p);
+}
+
+template <int S>
+int occupancy(dim3 block) {
+  int a = 0, b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, step_kernel<S, false>, block.x * block.y, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<S, true>, block.x * block.y, 0);
+  return std::max(1, std::min(a, b));
+}
+
+template <int S>
+void launch_init(const lbm_ctx* c) {
+  InitParams ip;
+  ip.f = c->fbuf(c->cur);
+  ip.nx = c->grid.nx; ip.ny = c->grid.ny; ip.nz = c->grid.nz;
+  ip.pitch = c->pitch; ip.plane = c->plane;
+  ip.u_prof = c->uprof_dev();
+  ip.seed = c->seed;
+  ip.amp = c->init_perturb;
+  init_kernel<S><<<c->sm_count * 8, 256, 0, c->stream>>>(ip);
+}
+
+template <int S>
+void launch_mass(const lbm_ctx* c) {
+  mass_partial_kernel<S><<<kMassBlocks, 256, 0, c->stream>>>(
+      c->fbuf(c->cur), c->grid.nx, c->pitch, (long long)c->grid.ny * c->grid.nz, c->plane,
+      c->mass_buf());
+  mass_final_kernel<<<1, 32, 0, c->stream>>>(c->mass_buf(), kMassBlocks, (double)c->cells,
+                                              c->mass_buf() + kMassBlocks);
+}
+
+template <int S>
+void launch_macro(const lbm_ctx* c, const StepParams& p, float* out) {
+  macro_kernel<S><<<c->sm_count * 8, 256, 0, c->stream>>>(p, out);
+}
+
+lbm_status check_device(lbm_ctx* c) {
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaGetLastError());
+  unsigned int flag = 0;
+  CK(c, cudaMemcpy(&flag, &c->state()->nan_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+  if (flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density or velocity");
+  return LBM_OK;
+}
+
+#define READY(c)                                   \
+  do {                                             \
+    if (!(c)) return LBM_ERR_ARG;                  \
+    if ((c)->status != LBM_OK) return LBM_ERR_STATE; \
+  } while (0)
+
+template <typename Fn>
+void dispatch(int storage, Fn&& fn) {
+  if (storage == LBM_F32) fn(std::integral_constant<int, 0>());
+  else if (storage == LBM_F16_SHIFTED) fn(std::integral_constant<int, 1>());
+  else fn(std::integral_constant<int, 2>());
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t k = 0; k < n; k++) {
+    h ^= p[k];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t storage, int32_t stats_xbins) {
+  if (!grid_ok(grid) || storage < 0 || storage > 2 || stats_xbins < 1 ||
+      stats_xbins > MAX_XBINS || stats_xbins > grid->nx)
+    return 0;
+  return layout_of(*grid, storage, stats_xbins).total;
+}
+
+lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double* lad,
+                      const lbm_forcing* forcing, int32_t storage, int32_t stats_xbins,
+                      uint64_t seed, double init_perturb, void* workspace,
+                      size_t workspace_bytes, lbm_ctx** out) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  const size_t need = lbm_workspace_bytes(grid, storage, stats_xbins);
+  if (need == 0 || !forcing || !(tau0 > 0.5) || !(cs >= 0.0) || !std::isfinite(tau0) ||
+      !std::isfinite(cs) || !std::isfinite(init_perturb))
+    return LBM_ERR_ARG;
+  if (forcing->u_bulk_target > 0.0 && !(forcing->ctrl_gain >= 0.0)) return LBM_ERR_ARG;
+  if (grid->x_lo == LBM_BC_INFLOW && !forcing->u_in_profile) return LBM_ERR_ARG;
+  if (workspace && workspace_bytes < need) return LBM_ERR_OOM;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LBM_ERR_ARG;
+
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  c->grid = *grid;
+  c->storage = storage;
+  c->nbins = stats_xbins;
+  c->tau0 = tau0;
+  c->cs = cs;
+  c->forcing = *forcing;
+  c->forcing.u_in_profile = nullptr;
+  if (lad) c->lad.assign(lad, lad + grid->ny);
+  c->uprof.assign(grid->ny, 0.0);
+  if (forcing->u_in_profile) c->uprof.assign(forcing->u_in_profile, forcing->u_in_profile + grid->ny);
+  c->seed = seed;
+  c->init_perturb = init_perturb;
+  c->pitch = pitch_of(grid->nx);
+  c->plane = (long long)grid->ny * grid->nz * c->pitch;
+  c->cells = (long long)grid->nx * grid->ny * grid->nz;
+  c->L = layout_of(*grid, storage, stats_xbins);
+
+  auto bail = [&](lbm_status s) {
+    if (c->owns_ws && c->ws) cudaFree(c->ws);
+    delete c;
+    return s;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return bail(LBM_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return bail(LBM_ERR_CUDA);
+  if (workspace) {
+    c->ws = static_cast<char*>(workspace);
+  } else {
+    if (cudaMalloc(&c->ws, c->L.total) != cudaSuccess) {
+      cudaGetLastError();
+      c->ws = nullptr;
+      return bail(LBM_ERR_OOM);
+    }
+    c->owns_ws = true;
+  }
+
+  // launch shape: a row of up to 256 cells per warp group, rows of z stacked
+  const int tx = std::min(256, (grid->nx + 31) / 32 * 32);
+  const int ry = std::max(1, 256 / tx);
+  c->block = dim3(tx, ry, 1);
+  c->nxc = (grid->nx + tx - 1) / tx;
+  c->nzg = (grid->nz + ry - 1) / ry;
+  dispatch(storage, [&](auto s) { c->blocks_per_sm = occupancy<decltype(s)::value>(c->block); });
+
+  // boundary tables and inputs
+  std::vector<float> kd(grid->ny, 0.f), fin((size_t)NQ * grid->ny, 0.f);
+  for (int y = 0; y < grid->ny; y++) {
+    if (!c->lad.empty()) kd[y] = (float)(forcing->cd * c->lad[y]);
+    const double u[3] = {c->uprof[y], 0.0, 0.0};
+    double fs[NQ];
+    feq_shift(u, fs);
+    for (int i = 0; i < NQ; i++) fin[(size_t)y * NQ + i] = (float)fs[i];
+  }
+  if (cudaMemsetAsync(c->ws, 0, c->L.total, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->kdrag(), kd.data(), sizeof(float) * grid->ny, cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->feq_in(), fin.data(), sizeof(float) * fin.size(),
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->uprof_dev(), c->uprof.data(), sizeof(double) * grid->ny,
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return bail(LBM_ERR_CUDA);
+  dispatch(storage, [&](auto s) { launch_init<decltype(s)::value>(c); });
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(LBM_ERR_CUDA);
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
+  READY(c);
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int32_t n) {
+  READY(c);
+  if (n < 0) return arg_error(c, "lbm_step: n < 0");
+  for (int32_t k = 0; k < n; k++) {
+    const StepParams p = make_params(c);
+    dispatch(c->storage, [&](auto s) { launch_step<decltype(s)::value>(c, p, c->stats_on); });
+    CK(c, cudaGetLastError());
+    c->last_grid = step_grid(c);
+    c->cur = 1 - c->cur;
+    c->steps++;
+    if (c->stats_on) c->stats_samples++;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+  READY(c);
+  return check_device(c);
+}
+
+lbm_status lbm_stats_reset(lbm_ctx* c, int32_t enable) {
+  READY(c);
+  CK(c, cudaMemsetAsync(c->stats(), 0, sizeof(double) * 9 * c->nbins * c->grid.ny, c->stream));
+  c->stats_on = enable != 0;
+  c->stats_samples = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
+  READY(c);
+  const int ny = c->grid.ny, nb = c->nbins, nx = c->grid.nx;
+  const size_t m = (size_t)nb * ny;
+  if (!out || n < 9 * m) return arg_error(c, "lbm_stats: output too small");
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  std::vector<double> acc(9 * m);
+  CK(c, cudaMemcpy(acc.data(), c->stats(), sizeof(double) * acc.size(), cudaMemcpyDeviceToHost));
+  std::vector<long long> width(nb, 0);
+  for (int x = 0; x < nx; x++) width[(long long)x * nb / nx]++;
+  for (int b = 0; b < nb; b++)
+    for (int y = 0; y < ny; y++) {
+      const size_t k = (size_t)b * ny + y;
+      const double cnt = (double)c->stats_samples * (double)c->grid.nz * (double)width[b];
+      const double inv = cnt > 0 ? 1.0 / cnt : 0.0;
+      const double mu = acc[0 * m + k] * inv, mv = acc[1 * m + k] * inv, mw = acc[2 * m + k] * inv;
+      out[0 * m + k] = mu;
+      out[1 * m + k] = mv;
+      out[2 * m + k] = mw;
+      out[3 * m + k] = acc[3 * m + k] * inv - mu * mu;
+      out[4 * m + k] = acc[4 * m + k] * inv - mv * mv;
+      out[5 * m + k] = acc[5 * m + k] * inv - mw * mw;
+      out[6 * m + k] = acc[6 * m + k] * inv - mu * mv;
+      out[7 * m + k] = acc[7 * m + k] * inv - mu * mw;
+      out[8 * m + k] = acc[8 * m + k] * inv - mv * mw;
+    }
+  if (samples) *samples = c->stats_samples;
+  return LBM_OK;
+}
+
+lbm_status lbm_mass(lbm_ctx* c, double* out) {
+  READY(c);
+  if (!out) return arg_error(c, "lbm_mass: out is NULL");
+  dispatch(c->storage, [&](auto s) { launch_mass<decltype(s)::value>(c); });
+  CK(c, cudaGetLastError());
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  CK(c, cudaMemcpy(out, c->mass_buf() + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_f(lbm_ctx* c, double* host, size_t n) {
+  READY(c);
+  if (!host || n != (size_t)NQ * c->cells) return arg_error(c, "lbm_get_f: wrong size");
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  const size_t eb = elem_bytes(c->storage);
+  std::vector<unsigned char> raw((size_t)NQ * c->plane * eb);
+  CK(c, cudaMemcpy(raw.data(), c->fbuf(c->cur), raw.size(), cudaMemcpyDeviceToHost));
+  const lbm_grid& g = c->grid;
+  for (int i = 0; i < NQ; i++)
+    for (int z = 0; z < g.nz; z++)
+      for (int y = 0; y < g.ny; y++)
+        for (int x = 0; x < g.nx; x++) {
+          const size_t dk = (size_t)i * c->plane + ((size_t)y * g.nz + z) * c->pitch + x;
+          double v;
+          if (c->storage == LBM_F32) v = reinterpret_cast<const float*>(raw.data())[dk];
+          else if (c->storage == LBM_F16_SHIFTED)
+            v = __half2float(reinterpret_cast<const __half*>(raw.data())[dk]);
+          else v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(raw.data())[dk]);
+          host[(((size_t)i * g.nz + z) * g.ny + y) * g.nx + x] = wgt_d(i) + v;
+        }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_f(lbm_ctx* c, const double* host, size_t n) {
+  READY(c);
+  if (!host || n != (size_t)NQ * c->cells) return arg_error(c, "lbm_set_f: wrong size");
+  CK(c, cudaStreamSynchronize(c->stream));
+  const size_t eb = elem_bytes(c->storage);
+  std::vector<unsigned char> raw((size_t)NQ * c->plane * eb, 0);
+  const lbm_grid& g = c->grid;
+  for (int i = 0; i < NQ; i++)
+    for (int z = 0; z < g.nz; z++)
+      for (int y = 0; y < g.ny; y++)
+        for (int x = 0; x < g.nx; x++) {
+          const size_t dk = (size_t)i * c->plane + ((size_t)y * g.nz + z) * c->pitch + x;
+          const double v = host[(((size_t)i * g.nz + z) * g.ny + y) * g.nx + x] - wgt_d(i);
+          if (c->storage == LBM_F32) reinterpret_cast<float*>(raw.data())[dk] = (float)v;
+          else if (c->storage == LBM_F16_SHIFTED)
+            reinterpret_cast<__half*>(raw.data())[dk] = Store<1>::from_double(v);
+          else reinterpret_cast<__nv_bfloat16*>(raw.data())[dk] = Store<2>::from_double(v);
+        }
+  CK(c, cudaMemcpy(c->fbuf(c->cur), raw.data(), raw.size(), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_macro(lbm_ctx* c, double* rho, double* u, size_t n) {
+  READY(c);
+  if (!rho || !u || n != (size_t)c->cells) return arg_error(c, "lbm_get_macro: wrong size");
+  if (!c->macro_buf) {
+    if (cudaMalloc(&c->macro_buf, sizeof(float) * 4 * c->cells) != cudaSuccess) {
+      cudaGetLastError();
+      c->macro_buf = nullptr;
+      return fail(c, LBM_ERR_OOM, "lbm_get_macro: cudaMalloc of the field buffer failed");
+    }
+  }
+  const StepParams p = make_params(c);
+  dispatch(c->storage, [&](auto s) { launch_macro<decltype(s)::value>(c, p, c->macro_buf); });
+  CK(c, cudaGetLastError());
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  std::vector<float> h((size_t)4 * c->cells);
+  CK(c, cudaMemcpy(h.data(), c->macro_buf, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+  for (long long k = 0; k < c->cells; k++) rho[k] = h[k];
+  for (long long k = 0; k < 3 * c->cells; k++) u[k] = h[c->cells + k];
+  return LBM_OK;
+}
+
+lbm_status lbm_drive(lbm_ctx* c, double g[3], double* u_bulk) {
+  READY(c);
+  if (!g || !u_bulk) return arg_error(c, "lbm_drive: NULL output");
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  double ub = 0.0;
+  if (c->steps > 0) {
+    std::vector<double> part(c->last_grid);
+    CK(c, cudaMemcpy(part.data(), c->ub_part() + (size_t)((c->steps + 1) % 2) * MAX_BLOCKS,
+                     sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
+    for (double v : part) ub += v;  // same order as the kernel's sum
+    ub /= (double)c->cells;
+  }
+  for (int a = 0; a < 3; a++) g[a] = c->forcing.g[a];
+  if (c->forcing.u_bulk_target > 0.0 && c->steps > 0)
+    g[0] = c->forcing.g[0] + c->forcing.ctrl_gain * (c->forcing.u_bulk_target - ub);
+  *u_bulk = ub;
+  return LBM_OK;
+}
+
+// ---- checkpoint ----------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, storage, nbins, pad;
+  lbm_grid grid;
+  int64_t steps, stats_samples;
+  int32_t stats_on, last_grid;
+  uint64_t payload_bytes, checksum;
+};
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+  READY(c);
+  if (!path) return arg_error(c, "lbm_save: path is NULL");
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  const size_t fb = (size_t)NQ * c->plane * elem_bytes(c->storage);
+  const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
+  const size_t ub = sizeof(double) * 2 * MAX_BLOCKS;
+  std::vector<unsigned char> payload(fb + sb + ub);
+  CK(c, cudaMemcpy(payload.data(), c->fbuf(c->cur), fb, cudaMemcpyDeviceToHost));
+  CK(c, cudaMemcpy(payload.data() + fb, c->stats(), sb, cudaMemcpyDeviceToHost));
+  CK(c, cudaMemcpy(payload.data() + fb + sb, c->ub_part(), ub, cudaMemcpyDeviceToHost));
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "LBMB300\0", 8);
+  h.version = 1;
+  h.storage = c->storage;
+  h.nbins = c->nbins;
+  h.grid = c->grid;
+  h.steps = c->steps;
+  h.stats_samples = c->stats_samples;
+  h.stats_on = c->stats_on;
+  h.last_grid = c->last_grid;
+  h.payload_bytes = payload.size();
+  h.checksum = fnv1a(payload.data(), payload.size());
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) {
+    c->err = std::string("lbm_save: cannot open ") + path;
+    return LBM_ERR_IO;
+  }
+  const bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 &&
+                  std::fwrite(payload.data(), 1, payload.size(), fp) == payload.size();
+  const bool closed = std::fclose(fp) == 0;
+  if (!ok || !closed) {
+    c->err = "lbm_save: write failed";
+    return LBM_ERR_IO;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+  READY(c);
+  if (!path) return arg_error(c, "lbm_load: path is NULL");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) {
+    c->err = std::string("lbm_load: cannot open ") + path;
+    return LBM_ERR_IO;
+  }
+  CkptHeader h;
+  const size_t fb = (size_t)NQ * c->plane * elem_bytes(c->storage);
+  const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
+  const size_t ub = sizeof(double) * 2 * MAX_BLOCKS;
+  std::vector<unsigned char> payload;
+  bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, "LBMB300\0", 8) == 0 &&
+            h.version == 1 && h.storage == c->storage && h.nbins == c->nbins &&
+            std::memcmp(&h.grid, &c->grid, sizeof(lbm_grid)) == 0 &&
+            h.payload_bytes == fb + sb + ub && h.last_grid >= 0 && h.last_grid <= MAX_BLOCKS;
+  if (ok) {
+    payload.resize(h.payload_bytes);
+    ok = std::fread(payload.data(), 1, payload.size(), fp) == payload.size() &&
+         fnv1a(payload.data(), payload.size()) == h.checksum;
+  }
+  std::fclose(fp);
+  if (!ok) {
+    c->err = "lbm_load: header mismatch, truncated file or checksum error";
+    return LBM_ERR_IO;
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaMemcpy(c->fbuf(0), payload.data(), fb, cudaMemcpyHostToDevice));
+  CK(c, cudaMemcpy(c->stats(), payload.data() + fb, sb, cudaMemcpyHostToDevice));
+  CK(c, cudaMemcpy(c->ub_part(), payload.data() + fb + sb, ub, cudaMemcpyHostToDevice));
+  c->cur = 0;
+  c->last_grid = h.last_grid;
+  c->steps = h.steps;
+  c->stats_samples = h.stats_samples;
+  c->stats_on = h.stats_on != 0;
+  return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->macro_buf) cudaFree(c->macro_buf);
+  if (c->owns_ws && c->ws) cudaFree(c->ws);
+  delete c;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+const char* lbm_status_string(int32_t s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_NAN: return "non-finite value in the flow field";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+    case LBM_ERR_STATE: return "context holds an earlier error";
+    case LBM_ERR_IO: return "checkpoint I/O error";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/lbm.h, sizes its workspace as documented and rejects
+invalid arguments before touching the device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2206_15454_b300 as P
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    P.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lbm_[a-z_0-9]+)", out))
+    declared = header_functions()
+    assert len(declared) >= 18
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    for n in declared:
+        assert hasattr(P.lib(), n)
+        assert hasattr(P, n) or n in ("lbm_last_error", "lbm_status_string")
+
+
+def _grid(nx=64, ny=32, nz=16, bc=(0, 0, 1, 2, 0, 0)):
+    return P.LbmGrid(nx, ny, nz, *bc)
+
+
+def test_workspace_bytes():
+    g = _grid()
+    n32 = P.lbm_workspace_bytes(g, P.LBM_F32, 1)
+    n16 = P.lbm_workspace_bytes(g, P.LBM_F16_SHIFTED, 1)
+    pops32 = 2 * 19 * 64 * 32 * 16 * 4
+    assert pops32 <= n32 < pops32 + 128 * 1024
+    assert n32 - n16 >= pops32 // 2 - 4096
+    # rows are padded to 64 elements
+    assert P.lbm_workspace_bytes(_grid(nx=65), P.LBM_F32, 1) >= 2 * 19 * 128 * 32 * 16 * 4
+
+
+@pytest.mark.parametrize("grid,storage,bins", [
+    (dict(nx=0), 0, 1),
+    (dict(bc=(4, 0, 1, 2, 0, 0)), 0, 1),        # inflow without outflow
+    (dict(bc=(0, 0, 2, 2, 0, 0)), 0, 1),        # free-slip bottom unsupported
+    (dict(bc=(0, 0, 1, 2, 1, 1)), 0, 1),        # walls in z unsupported
+    (dict(), 3, 1),                              # unknown storage
+    (dict(), 0, 0),                              # no statistics bin
+    (dict(nx=8), 0, 9),                          # more bins than columns
+    (dict(nx=4096, ny=4096, nz=256), 0, 1),      # beyond 2^31 cells
+])
+def test_invalid_grids_rejected(grid, storage, bins):
+    assert P.lbm_workspace_bytes(_grid(**grid), storage, bins) == 0
+
+
+def test_create_rejects_bad_arguments_without_a_device():
+    g = _grid()
+    fo = P.LbmForcing()
+    ctx = C.c_void_p()
+    L = P.lib()
+    # tau0 <= 1/2 is unstable by construction (negative viscosity)
+    s = L.lbm_create(C.byref(g), 0.5, 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0, None, 0,
+                     C.byref(ctx))
+    assert s == P.LBM_ERR_ARG and not ctx.value
+    s = L.lbm_create(C.byref(g), float("nan"), 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0, None, 0,
+                     C.byref(ctx))
+    assert s == P.LBM_ERR_ARG
+    # inflow needs a profile
+    gi = _grid(bc=(4, 5, 1, 2, 0, 0))
+    s = L.lbm_create(C.byref(gi), 0.6, 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0, None, 0,
+                     C.byref(ctx))
+    assert s == P.LBM_ERR_ARG
+    # a workspace smaller than lbm_workspace_bytes
+    s = L.lbm_create(C.byref(g), 0.6, 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0,
+                     C.c_void_p(4096), 16, C.byref(ctx))
+    assert s == P.LBM_ERR_OOM
+    assert L.lbm_create(C.byref(g), 0.6, 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0, None, 0,
+                        None) == P.LBM_ERR_ARG
+
+
+def test_null_context_calls_fail_cleanly():
+    L = P.lib()
+    assert L.lbm_step(None, 1) == P.LBM_ERR_ARG
+    assert L.lbm_sync(None) == P.LBM_ERR_ARG
+    assert L.lbm_steps_done(None) == -1
+    L.lbm_destroy(None)
+    assert L.lbm_status_string(P.LBM_ERR_NAN).decode().startswith("non-finite")
+    assert L.lbm_last_error(None).decode() == "no context"
+
+
+def test_structs_match_the_header():
+    # lbm_grid: 9 int32; lbm_forcing: 3+1 doubles, 2 int32, 2+3 doubles, 1 pointer
+    assert C.sizeof(P.LbmGrid) == 36
+    assert C.sizeof(P.LbmForcing) == 8 * 4 + 8 + 8 * 5 + 8
