@@ -2,16 +2,19 @@
 //
 // Owns the context (grid, parameters, device buffers carved from one
 // workspace), enqueues the kernels of lbm_device.cuh on the context's stream,
-// and converts populations between the device storage ([q][y][z][x], shifted
-// by the lattice weights, FP32/FP16/BF16) and the public FP64 layout
-// ([q][z][y][x], unshifted).  No lattice Boltzmann arithmetic runs on the host.
+// and converts populations between the device storage (row-interleaved
+// [y][z][x-chunk][q][x], shifted by the lattice weights, FP32/FP16/BF16) and
+// the public FP64 layout ([q][z][y][x], unshifted).  No lattice Boltzmann
+// arithmetic runs on the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -28,7 +31,25 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
 
-int pitch_of(int nx) { return (nx + 63) / 64 * 64; }
+// chunk width: the smallest of 64, 128, 256 cells that covers a row, else 256
+int chunk_width(int nx) { return nx <= 64 ? 64 : (nx <= 128 ? 128 : 256); }
+
+struct Shape {
+  int xt, nxc, g, xtp;  // chunk width, chunks per row, ghost line, direction-row length
+  long long row;        // elements per chunk-row (19 direction rows)
+  long long elems;      // elements per population set
+};
+
+Shape shape_of(const lbm_grid& gr, int storage) {
+  Shape s;
+  s.xt = chunk_width(gr.nx);
+  s.nxc = (gr.nx + s.xt - 1) / s.xt;
+  s.g = 128 / (int)elem_bytes(storage);
+  s.xtp = s.xt + 2 * s.g;
+  s.row = (long long)NQ * s.xtp;
+  s.elems = (long long)gr.ny * gr.nz * s.nxc * s.row;
+  return s;
+}
 
 struct Layout {
   size_t f_bytes, stats_off, state_off, ubpart_off, kdrag_off, feqin_off, uprof_off, mass_off,
@@ -37,8 +58,8 @@ struct Layout {
 
 Layout layout_of(const lbm_grid& g, int storage, int nbins) {
   Layout L;
-  const size_t plane = (size_t)g.ny * g.nz * pitch_of(g.nx);
-  L.f_bytes = align_up(plane * NQ * elem_bytes(storage), kAlign);
+  const Shape s = shape_of(g, storage);
+  L.f_bytes = align_up((size_t)s.elems * elem_bytes(storage), kAlign);
   size_t off = 2 * L.f_bytes;
   L.stats_off = off;  off += align_up(sizeof(double) * 9 * nbins * g.ny, kAlign);
   L.state_off = off;  off += align_up(sizeof(DevState), kAlign);
@@ -53,7 +74,7 @@ Layout layout_of(const lbm_grid& g, int storage, int nbins) {
 
 bool grid_ok(const lbm_grid* g) {
   if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1) return false;
-  const long long cells = (long long)pitch_of(g->nx) * g->ny * g->nz;
+  const long long cells = (long long)g->nx * g->ny * g->nz;
   if (cells >= (1ll << 31)) return false;
   const bool xper = g->x_lo == LBM_BC_PERIODIC && g->x_hi == LBM_BC_PERIODIC;
   const bool xio = g->x_lo == LBM_BC_INFLOW && g->x_hi == LBM_BC_OUTFLOW;
@@ -75,8 +96,8 @@ struct lbm_ctx {
   std::vector<double> lad, uprof;
   uint64_t seed = 0;
   double init_perturb = 0;
-  int pitch = 0;
-  long long plane = 0, cells = 0;
+  Shape sh;
+  long long cells = 0;
   Layout L;
   char* ws = nullptr;
   bool owns_ws = false;
@@ -88,8 +109,10 @@ struct lbm_ctx {
   float* macro_buf = nullptr;
   int sm_count = 0, blocks_per_sm = 0;
   int last_grid = 0;          // blocks of the previous step launch (partials to sum)
+  int nstage = 0;             // tiles in flight per block
+  size_t stage_smem = 0;      // dynamic shared memory per block
   dim3 block;
-  int nxc = 0, nzg = 0;
+  int nzg = 0;
   lbm_status status = LBM_OK;
   std::string err;
 
@@ -101,6 +124,11 @@ struct lbm_ctx {
   float* feq_in() const { return reinterpret_cast<float*>(ws + L.feqin_off); }
   double* uprof_dev() const { return reinterpret_cast<double*>(ws + L.uprof_off); }
   double* mass_buf() const { return reinterpret_cast<double*>(ws + L.mass_off); }
+  // device element index of population q at cell (x, y, z)
+  long long dev_index(int q, int x, int y, int z) const {
+    return (((long long)y * grid.nz + z) * sh.nxc + x / sh.xt) * sh.row + (long long)q * sh.xtp +
+           sh.g + x % sh.xt;
+  }
 };
 
 namespace {
@@ -138,8 +166,7 @@ StepParams make_params(const lbm_ctx* c) {
   StepParams p;
   std::memset(&p, 0, sizeof(p));
   const lbm_grid& g = c->grid;
-  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.pitch = c->pitch; p.plane = c->plane;
-  for (int i = 0; i < NQ; i++) p.qoff[i] = (long long)i * c->plane;
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.nxc = c->sh.nxc;
   p.x_io = g.x_lo == LBM_BC_INFLOW;
   p.y_walls = g.y_lo == LBM_BC_BOUNCEBACK;
   p.top = g.y_hi == LBM_BC_BOUNCEBACK ? 1 : g.y_hi == LBM_BC_FREESLIP ? 2 : 3;
@@ -160,13 +187,13 @@ StepParams make_params(const lbm_ctx* c) {
   p.canopy_x0 = c->forcing.x_canopy_begin;
   p.canopy_x1 = c->forcing.x_canopy_end;
   p.kdrag = c->lad.empty() ? nullptr : c->kdrag();
-  p.feq_in = p.x_io ? c->feq_in() : nullptr;
+  p.feq_in = c->feq_in();
   double ft[NQ];
   feq_shift(c->forcing.u_top, ft);
   for (int i = 0; i < NQ; i++) p.feq_top[i] = (float)ft[i];
-  p.nxc = c->nxc;
   p.nzg = c->nzg;
-  p.ntiles = (long long)c->nxc * c->nzg * g.ny;
+  p.ntiles = (long long)c->sh.nxc * c->nzg * g.ny;
+  p.nstage = c->nstage;
   p.stats = c->stats();
   p.nbins = c->nbins;
   p.state = c->state();
@@ -175,76 +202,107 @@ StepParams make_params(const lbm_ctx* c) {
   return p;
 }
 
+// Instantiate a functor over (chunk width, storage type).
+template <typename Fn>
+void dispatch(const lbm_ctx* c, Fn&& fn) {
+  auto by_storage = [&](auto xt) {
+    if (c->storage == LBM_F32) fn(xt, std::integral_constant<int, 0>());
+    else if (c->storage == LBM_F16_SHIFTED) fn(xt, std::integral_constant<int, 1>());
+    else fn(xt, std::integral_constant<int, 2>());
+  };
+  if (c->sh.xt == 64) by_storage(std::integral_constant<int, 64>());
+  else if (c->sh.xt == 128) by_storage(std::integral_constant<int, 128>());
+  else by_storage(std::integral_constant<int, 256>());
+}
+
 int step_grid(const lbm_ctx* c) {
-  const long long ntiles = (long long)c->nxc * c->nzg * c->grid.ny;
+  const long long ntiles = (long long)c->sh.nxc * c->nzg * c->grid.ny;
   const long long want = (long long)c->sm_count * c->blocks_per_sm;
   return (int)std::max<long long>(1, std::min<long long>({want, ntiles, (long long)MAX_BLOCKS}));
 }
 
-template <int S>
+template <int XT, int S>
 void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
   const int grid = step_grid(c);
   if (stats)
-    step_kernel<S, true><<<grid, c->block, 0, c->stream>>>(p);
+    step_kernel<XT, S, true><<<grid, c->block, c->stage_smem, c->stream>>>(p);
   else
-    step_kernel<S, false><<<grid, c->block, 0, c->stream>>>(p);
+    step_kernel<XT, S, false><<<grid, c->block, c->stage_smem, c->stream>>>(p);
 }
 
-template <int S>
-int occupancy(dim3 block) {
+// Shared-memory stages: as many tiles in flight as fit beside three blocks
+// per SM (at most 8, at least 2).
+template <int XT, int S>
+void plan_stages(lbm_ctx* c) {
+  using St = Stage<XT, S>;
+  const size_t stage = (size_t)c->block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
+  c->nstage = (int)std::max<size_t>(2, std::min<size_t>(8, (70 * 1024) / stage));
+  c->stage_smem = c->nstage * stage;
+  cudaFuncSetAttribute(step_kernel<XT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->stage_smem);
+  cudaFuncSetAttribute(step_kernel<XT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c->stage_smem);
+}
+
+template <int XT, int S>
+int occupancy(dim3 block, size_t smem) {
   int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, step_kernel<S, false>, block.x * block.y, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<S, true>, block.x * block.y, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, step_kernel<XT, S, false>, block.x * block.y, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<XT, S, true>, block.x * block.y, smem);
   return std::max(1, std::min(a, b));
 }
 
-template <int S>
+// Ghost slots of both population sets from their cells: the current set
+// needs all of them; the other keeps the inflow ghosts, which no step
+// rewrites (its other ghosts are written by the next step before any read).
+template <int XT, int S>
+void launch_ghosts(const lbm_ctx* c) {
+  StepParams p = make_params(c);
+  ghost_kernel<XT, S><<<c->sm_count * 4, 256, 0, c->stream>>>(p, c->fbuf(c->cur));
+  ghost_kernel<XT, S><<<c->sm_count * 4, 256, 0, c->stream>>>(p, c->fbuf(1 - c->cur));
+}
+
+template <int XT, int S>
 void launch_init(const lbm_ctx* c) {
   InitParams ip;
   ip.f = c->fbuf(c->cur);
-  ip.nx = c->grid.nx; ip.ny = c->grid.ny; ip.nz = c->grid.nz;
-  ip.pitch = c->pitch; ip.plane = c->plane;
+  ip.nx = c->grid.nx; ip.ny = c->grid.ny; ip.nz = c->grid.nz; ip.nxc = c->sh.nxc;
   ip.u_prof = c->uprof_dev();
   ip.seed = c->seed;
   ip.amp = c->init_perturb;
-  init_kernel<S><<<c->sm_count * 8, 256, 0, c->stream>>>(ip);
+  init_kernel<XT, S><<<c->sm_count * 8, 256, 0, c->stream>>>(ip);
+  launch_ghosts<XT, S>(c);
 }
 
-template <int S>
+template <int XT, int S>
 void launch_mass(const lbm_ctx* c) {
-  mass_partial_kernel<S><<<kMassBlocks, 256, 0, c->stream>>>(
-      c->fbuf(c->cur), c->grid.nx, c->pitch, (long long)c->grid.ny * c->grid.nz, c->plane,
-      c->mass_buf());
+  mass_partial_kernel<XT, S><<<kMassBlocks, 256, 0, c->stream>>>(
+      c->fbuf(c->cur), c->grid.nx, (long long)c->grid.ny * c->grid.nz, c->sh.nxc, c->mass_buf());
   mass_final_kernel<<<1, 32, 0, c->stream>>>(c->mass_buf(), kMassBlocks, (double)c->cells,
                                               c->mass_buf() + kMassBlocks);
 }
 
-template <int S>
+template <int XT, int S>
 void launch_macro(const lbm_ctx* c, const StepParams& p, float* out) {
-  macro_kernel<S><<<c->sm_count * 8, 256, 0, c->stream>>>(p, out);
+  macro_kernel<XT, S><<<c->sm_count * 8, 256, 0, c->stream>>>(p, out);
 }
 
 lbm_status check_device(lbm_ctx* c) {
   CK(c, cudaStreamSynchronize(c->stream));
   CK(c, cudaGetLastError());
-  unsigned int flag = 0;
-  CK(c, cudaMemcpy(&flag, &c->state()->nan_flag, sizeof(flag), cudaMemcpyDeviceToHost));
-  if (flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density or velocity");
+  DevState st;
+  CK(c, cudaMemcpy(&st, c->state(), sizeof(st), cudaMemcpyDeviceToHost));
+  if (st.timeout_flag)
+    return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
+  if (st.nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density or velocity");
   return LBM_OK;
 }
 
-#define READY(c)                                   \
-  do {                                             \
-    if (!(c)) return LBM_ERR_ARG;                  \
+#define READY(c)                                     \
+  do {                                               \
+    if (!(c)) return LBM_ERR_ARG;                    \
     if ((c)->status != LBM_OK) return LBM_ERR_STATE; \
   } while (0)
-
-template <typename Fn>
-void dispatch(int storage, Fn&& fn) {
-  if (storage == LBM_F32) fn(std::integral_constant<int, 0>());
-  else if (storage == LBM_F16_SHIFTED) fn(std::integral_constant<int, 1>());
-  else fn(std::integral_constant<int, 2>());
-}
 
 uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
@@ -295,8 +353,7 @@ lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double
   if (forcing->u_in_profile) c->uprof.assign(forcing->u_in_profile, forcing->u_in_profile + grid->ny);
   c->seed = seed;
   c->init_perturb = init_perturb;
-  c->pitch = pitch_of(grid->nx);
-  c->plane = (long long)grid->ny * grid->nz * c->pitch;
+  c->sh = shape_of(*grid, storage);
   c->cells = (long long)grid->nx * grid->ny * grid->nz;
   c->L = layout_of(*grid, storage, stats_xbins);
 
@@ -320,13 +377,14 @@ lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double
     c->owns_ws = true;
   }
 
-  // launch shape: a row of up to 256 cells per warp group, rows of z stacked
-  const int tx = std::min(256, (grid->nx + 31) / 32 * 32);
-  const int ry = std::max(1, 256 / tx);
-  c->block = dim3(tx, ry, 1);
-  c->nxc = (grid->nx + tx - 1) / tx;
-  c->nzg = (grid->nz + ry - 1) / ry;
-  dispatch(storage, [&](auto s) { c->blocks_per_sm = occupancy<decltype(s)::value>(c->block); });
+  // launch shape: a chunk of XT cells per row, 256 / XT rows (consecutive z) per block
+  c->block = dim3(c->sh.xt, 256 / c->sh.xt, 1);
+  c->nzg = (grid->nz + (int)c->block.y - 1) / (int)c->block.y;
+  dispatch(c, [&](auto xt, auto s) {
+    plan_stages<decltype(xt)::value, decltype(s)::value>(c);
+    c->blocks_per_sm = occupancy<decltype(xt)::value, decltype(s)::value>(c->block, c->stage_smem);
+  });
+  if (cudaGetLastError() != cudaSuccess) return bail(LBM_ERR_CUDA);
 
   // boundary tables and inputs
   std::vector<float> kd(grid->ny, 0.f), fin((size_t)NQ * grid->ny, 0.f);
@@ -345,7 +403,7 @@ lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double
       cudaMemcpyAsync(c->uprof_dev(), c->uprof.data(), sizeof(double) * grid->ny,
                       cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     return bail(LBM_ERR_CUDA);
-  dispatch(storage, [&](auto s) { launch_init<decltype(s)::value>(c); });
+  dispatch(c, [&](auto xt, auto s) { launch_init<decltype(xt)::value, decltype(s)::value>(c); });
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(LBM_ERR_CUDA);
   *out = c;
@@ -364,7 +422,9 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
   if (n < 0) return arg_error(c, "lbm_step: n < 0");
   for (int32_t k = 0; k < n; k++) {
     const StepParams p = make_params(c);
-    dispatch(c->storage, [&](auto s) { launch_step<decltype(s)::value>(c, p, c->stats_on); });
+    dispatch(c, [&](auto xt, auto s) {
+      launch_step<decltype(xt)::value, decltype(s)::value>(c, p, c->stats_on);
+    });
     CK(c, cudaGetLastError());
     c->last_grid = step_grid(c);
     c->cur = 1 - c->cur;
@@ -421,7 +481,7 @@ lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
 lbm_status lbm_mass(lbm_ctx* c, double* out) {
   READY(c);
   if (!out) return arg_error(c, "lbm_mass: out is NULL");
-  dispatch(c->storage, [&](auto s) { launch_mass<decltype(s)::value>(c); });
+  dispatch(c, [&](auto xt, auto s) { launch_mass<decltype(xt)::value, decltype(s)::value>(c); });
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
@@ -435,14 +495,14 @@ lbm_status lbm_get_f(lbm_ctx* c, double* host, size_t n) {
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
   const size_t eb = elem_bytes(c->storage);
-  std::vector<unsigned char> raw((size_t)NQ * c->plane * eb);
+  std::vector<unsigned char> raw((size_t)c->sh.elems * eb);
   CK(c, cudaMemcpy(raw.data(), c->fbuf(c->cur), raw.size(), cudaMemcpyDeviceToHost));
   const lbm_grid& g = c->grid;
   for (int i = 0; i < NQ; i++)
     for (int z = 0; z < g.nz; z++)
       for (int y = 0; y < g.ny; y++)
         for (int x = 0; x < g.nx; x++) {
-          const size_t dk = (size_t)i * c->plane + ((size_t)y * g.nz + z) * c->pitch + x;
+          const size_t dk = (size_t)c->dev_index(i, x, y, z);
           double v;
           if (c->storage == LBM_F32) v = reinterpret_cast<const float*>(raw.data())[dk];
           else if (c->storage == LBM_F16_SHIFTED)
@@ -458,13 +518,13 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* host, size_t n) {
   if (!host || n != (size_t)NQ * c->cells) return arg_error(c, "lbm_set_f: wrong size");
   CK(c, cudaStreamSynchronize(c->stream));
   const size_t eb = elem_bytes(c->storage);
-  std::vector<unsigned char> raw((size_t)NQ * c->plane * eb, 0);
+  std::vector<unsigned char> raw((size_t)c->sh.elems * eb, 0);
   const lbm_grid& g = c->grid;
   for (int i = 0; i < NQ; i++)
     for (int z = 0; z < g.nz; z++)
       for (int y = 0; y < g.ny; y++)
         for (int x = 0; x < g.nx; x++) {
-          const size_t dk = (size_t)i * c->plane + ((size_t)y * g.nz + z) * c->pitch + x;
+          const size_t dk = (size_t)c->dev_index(i, x, y, z);
           const double v = host[(((size_t)i * g.nz + z) * g.ny + y) * g.nx + x] - wgt_d(i);
           if (c->storage == LBM_F32) reinterpret_cast<float*>(raw.data())[dk] = (float)v;
           else if (c->storage == LBM_F16_SHIFTED)
@@ -472,6 +532,9 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* host, size_t n) {
           else reinterpret_cast<__nv_bfloat16*>(raw.data())[dk] = Store<2>::from_double(v);
         }
   CK(c, cudaMemcpy(c->fbuf(c->cur), raw.data(), raw.size(), cudaMemcpyHostToDevice));
+  dispatch(c, [&](auto xt, auto s) { launch_ghosts<decltype(xt)::value, decltype(s)::value>(c); });
+  CK(c, cudaGetLastError());
+  CK(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
 
@@ -486,7 +549,9 @@ lbm_status lbm_get_macro(lbm_ctx* c, double* rho, double* u, size_t n) {
     }
   }
   const StepParams p = make_params(c);
-  dispatch(c->storage, [&](auto s) { launch_macro<decltype(s)::value>(c, p, c->macro_buf); });
+  dispatch(c, [&](auto xt, auto s) {
+    launch_macro<decltype(xt)::value, decltype(s)::value>(c, p, c->macro_buf);
+  });
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
@@ -507,7 +572,7 @@ lbm_status lbm_drive(lbm_ctx* c, double g[3], double* u_bulk) {
     std::vector<double> part(c->last_grid);
     CK(c, cudaMemcpy(part.data(), c->ub_part() + (size_t)((c->steps + 1) % 2) * MAX_BLOCKS,
                      sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
-    for (double v : part) ub += v;  // same order as the kernel's sum
+    for (double v : part) ub += v;
     ub /= (double)c->cells;
   }
   for (int a = 0; a < 3; a++) g[a] = c->forcing.g[a];
@@ -534,7 +599,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   if (!path) return arg_error(c, "lbm_save: path is NULL");
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
-  const size_t fb = (size_t)NQ * c->plane * elem_bytes(c->storage);
+  const size_t fb = (size_t)c->sh.elems * elem_bytes(c->storage);
   const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
   const size_t ub = sizeof(double) * 2 * MAX_BLOCKS;
   std::vector<unsigned char> payload(fb + sb + ub);
@@ -544,7 +609,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "LBMB300\0", 8);
-  h.version = 1;
+  h.version = 2;
   h.storage = c->storage;
   h.nbins = c->nbins;
   h.grid = c->grid;
@@ -578,12 +643,12 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     return LBM_ERR_IO;
   }
   CkptHeader h;
-  const size_t fb = (size_t)NQ * c->plane * elem_bytes(c->storage);
+  const size_t fb = (size_t)c->sh.elems * elem_bytes(c->storage);
   const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
   const size_t ub = sizeof(double) * 2 * MAX_BLOCKS;
   std::vector<unsigned char> payload;
   bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, "LBMB300\0", 8) == 0 &&
-            h.version == 1 && h.storage == c->storage && h.nbins == c->nbins &&
+            h.version == 2 && h.storage == c->storage && h.nbins == c->nbins &&
             std::memcmp(&h.grid, &c->grid, sizeof(lbm_grid)) == 0 &&
             h.payload_bytes == fb + sb + ub && h.last_grid >= 0 && h.last_grid <= MAX_BLOCKS;
   if (ok) {
@@ -601,10 +666,10 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
   CK(c, cudaMemcpy(c->stats(), payload.data() + fb, sb, cudaMemcpyHostToDevice));
   CK(c, cudaMemcpy(c->ub_part(), payload.data() + fb + sb, ub, cudaMemcpyHostToDevice));
   c->cur = 0;
-  c->last_grid = h.last_grid;
   c->steps = h.steps;
   c->stats_samples = h.stats_samples;
   c->stats_on = h.stats_on != 0;
+  c->last_grid = h.last_grid;
   return LBM_OK;
 }
 

@@ -52,38 +52,58 @@ template <int S> struct Store;
 template <> struct Store<0> {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
+  static __device__ __forceinline__ float to_float(T v) { return v; }
   static __device__ __forceinline__ void st(T* p, float v) { *p = v; }
   static __host__ __device__ __forceinline__ T from_double(double v) { return (float)v; }
 };
 template <> struct Store<1> {
   using T = __half;
   static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float to_float(T v) { return __half2float(v); }
   static __device__ __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v); }
   static __host__ __device__ __forceinline__ T from_double(double v) { return __double2half(v); }
 };
 template <> struct Store<2> {
   using T = __nv_bfloat16;
   static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ float to_float(T v) { return __bfloat162float(v); }
   static __device__ __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
   static __host__ __device__ __forceinline__ T from_double(double v) { return __double2bfloat16(v); }
 };
 
 // ---- device-resident controller / health state --------------------------------
 struct DevState {
-  unsigned int nan_flag;    // set when a cell produced a non-finite value
-  unsigned int pad;
+  unsigned int nan_flag;      // set when a cell produced a non-finite value
+  unsigned int timeout_flag;  // set when a bounded device wait gave up
 };
 
 constexpr int MAX_BLOCKS = 4096;  // per-block bulk-velocity partials per slot
-
 constexpr int MAX_XBINS = 64;
+
+// ---- population layout in HBM ------------------------------------------------------
+// One population set is f[y][z][xc][q][XTP]: rows are cut into chunks of XT
+// cells (XT = 64, 128 or 256) and a chunk-row (y, z, xc) holds the 19
+// direction rows of the chunk back to back, each XTP = XT + 2G elements with
+// G one 128-byte line: cell x = xc*XT + tx sits in slot G + tx, on whole lines.
+// Slot G-1 holds, for the directions with c_x = +1, the value of the column
+// left of the chunk (previous chunk, periodic wrap, or the inflow
+// equilibrium); slot G + n (n = cells of the chunk) holds, for c_x = -1, the
+// column right of it (next chunk, periodic wrap, or a zero-gradient copy at
+// an outflow).  Cells on chunk edges refresh these ghost slots when they
+// store, so a tile's sources are exactly its staged rows: a direction row is
+// copied with the one ghost its c_x reads.
+template <int XT, int S>
+struct Geo {
+  using T = typename Store<S>::T;
+  static constexpr int G = 128 / (int)sizeof(T);
+  static constexpr int XTP = XT + 2 * G;
+  static constexpr int ROW = NQ * XTP;  // elements per chunk-row
+};
 
 struct StepParams {
   const void* src;
   void* dst;
-  int nx, ny, nz, pitch;
-  long long plane;          // elements per population plane (ny*nz*pitch)
-  long long qoff[NQ];       // q * plane: read from the parameter bank, not registers
+  int nx, ny, nz, nxc;      // nxc chunks of XT cells per row
   int x_io;                 // 1: inflow at x = 0, outflow at x = nx-1; 0: periodic
   int y_walls;              // 1: bounce-back bottom + `top` kind; 0: periodic
   int top;                  // 1 bounce-back, 2 free-slip, 3 equilibrium
@@ -96,117 +116,91 @@ struct StepParams {
   int slot_read, slot_write, nprev;  // nprev: blocks of the previous launch
   int canopy_x0, canopy_x1;
   const float* kdrag;       // ny values C_D a(y), or nullptr
-  const float* feq_in;      // [ny][19] shifted f_eq(1, u_in(y)) (inflow), or nullptr
+  const float* feq_in;      // [ny][19] shifted f_eq(1, u_in(y)) for the inflow column
   float feq_top[NQ];        // shifted f_eq(1, u_top) (equilibrium top)
-  // tiling: tile = (y, z-group, x-chunk); block = (tx, ry) threads
-  int nxc, nzg;
+  // tiling: tile = (y, z-group, x-chunk), block = (XT, ry) threads
+  int nzg;
   long long ntiles;
+  int nstage;               // tiles in flight per block
   // statistics
-  double* stats;            // [9][nbins][ny] FP64 sums, or nullptr when off
+  double* stats;            // [9][nbins][ny] FP64 sums
   int nbins;
   DevState* state;
 };
 
-// Source coordinates of direction i for a cell at (x, y, z): the caller
-// precomputes the per-axis neighbours once per cell.
-struct Nbr {
-  int xm, xp;   // source x for c_x = +1 (x-1) and c_x = -1 (x+1), after wrap/clamp
-  int zm, zp;   // source z for c_z = +1 and -1 (periodic)
-  int ym, yp;   // source y for c_y = +1 and -1 (periodic wrap or own row at walls)
-  bool inflow;  // x == 0 with an inflow boundary
-  bool lo_wall, hi_wall;
-};
-
-__device__ __forceinline__ Nbr neighbours(const StepParams& p, int x, int y, int z) {
-  Nbr n;
-  n.inflow = false;
-  n.xm = x - 1;
-  n.xp = x + 1;
-  if (x == 0) {
-    if (p.x_io) { n.xm = 0; n.inflow = true; } else { n.xm = p.nx - 1; }
-  }
-  if (x == p.nx - 1) n.xp = p.x_io ? p.nx - 1 : 0;   // outflow: zero-gradient copy
-  n.zm = (z == 0) ? p.nz - 1 : z - 1;
-  n.zp = (z == p.nz - 1) ? 0 : z + 1;
-  n.ym = y - 1;
-  n.yp = y + 1;
-  n.lo_wall = n.hi_wall = false;
-  if (y == 0) {
-    if (p.y_walls) { n.ym = 0; n.lo_wall = true; } else { n.ym = p.ny - 1; }
-  }
-  if (y == p.ny - 1) {
-    if (p.y_walls) { n.yp = y; n.hi_wall = true; } else { n.yp = 0; }
-  }
-  return n;
+// element index of population q at cell (x, y, z)
+template <int XT, int S>
+__device__ __forceinline__ long long pop_index(const StepParams& p, int q, int x, int y, int z) {
+  return ((long long)((y * p.nz + z) * p.nxc + x / XT) * NQ + q) * Geo<XT, S>::XTP + Geo<XT, S>::G +
+         x % XT;
 }
 
-template <int I>
-__device__ __forceinline__ int src_x(const Nbr& n, int x) { return cx(I) == 1 ? n.xm : cx(I) == -1 ? n.xp : x; }
-template <int I>
-__device__ __forceinline__ int src_y(const Nbr& n, int y) { return cy(I) == 1 ? n.ym : cy(I) == -1 ? n.yp : y; }
-template <int I>
-__device__ __forceinline__ int src_z(const Nbr& n, int z) { return cz(I) == 1 ? n.zm : cz(I) == -1 ? n.zp : z; }
+// Source of direction i for a cell at row (y, z): plane q, row (ys, zs), and
+// how it enters: shifted in x by -c_x (streaming), taken from the own column
+// (halfway bounce-back), or a constant (equilibrium top).  Streaming with the
+// y boundaries of Algorithm 1's "stream" step.
+enum : int { SRC_SHIFT = 0, SRC_OWN_X = 1, SRC_CONST = 2 };
 
-template <int S, int I>
-__device__ __forceinline__ float load_dir(const StepParams& p, const typename Store<S>::T* src,
-                                          const Nbr& n, int x, int y, int z) {
-  const int xs = src_x<I>(n, x), ys = src_y<I>(n, y), zs = src_z<I>(n, z);
-  const long long idx = p.qoff[I] + (long long)((ys * p.nz + zs) * p.pitch + xs);
-  return Store<S>::ld(src + idx);
-}
-
-template <int S, int I>
-__device__ __forceinline__ void pull_one(const StepParams& p, const typename Store<S>::T* src,
-                                         const Nbr& n, int x, int y, int z, float* f) {
-  float v = load_dir<S, I>(p, src, n, x, y, z);
-  // inflow: incoming populations at x = 0 are the inflow equilibrium
-  if (cx(I) == 1 && n.inflow) v = p.feq_in[src_y<I>(n, y) * NQ + I];
-  // bottom wall, halfway bounce-back: the population sent towards the wall returns
-  if (cy(I) == 1 && n.lo_wall) {
-    v = Store<S>::ld(src + p.qoff[opp(I)] + (long long)((y * p.nz + z) * p.pitch + x));
-  }
-  if (cy(I) == -1 && n.hi_wall) {
-    if (p.top == 1) {
-      v = Store<S>::ld(src + p.qoff[opp(I)] + (long long)((y * p.nz + z) * p.pitch + x));
+__device__ __forceinline__ int row_source(const StepParams& p, int i, int dy, int dz, int y, int z,
+                                          int& q, int& ys, int& zs) {
+  q = i;
+  ys = y - dy;
+  zs = z - dz;
+  if (zs < 0) zs += p.nz;
+  if (zs >= p.nz) zs -= p.nz;
+  if (ys < 0 || ys >= p.ny) {
+    if (!p.y_walls) {
+      ys = ys < 0 ? ys + p.ny : ys - p.ny;
+    } else if (ys < 0 || p.top == 1) {
+      q = (i == 0) ? 0 : ((i & 1) ? i + 1 : i - 1);  // bounce-back: own cell, reversed
+      ys = y;
+      zs = z;
+      return SRC_OWN_X;
     } else if (p.top == 2) {
-      // free slip: the mirrored population of the upstream column in x and z
-      constexpr int J = miry(I);
-      const int xs = src_x<I>(n, x), zs = src_z<I>(n, z);
-      v = Store<S>::ld(src + p.qoff[J] + (long long)((y * p.nz + zs) * p.pitch + xs));
-      if (cx(I) == 1 && n.inflow) v = p.feq_in[y * NQ + J];
+      q = miry(i);  // free slip: mirrored, upstream in x and z
+      ys = y;
     } else {
-      v = p.feq_top[I];
+      return SRC_CONST;  // equilibrium top
     }
   }
-  f[I] = v;
+  return SRC_SHIFT;
 }
 
-template <int S, int I = 0>
-__device__ __forceinline__ void pull_all(const StepParams& p, const typename Store<S>::T* src,
-                                         const Nbr& n, int x, int y, int z, float* f) {
-  if constexpr (I < NQ) {
-    pull_one<S, I>(p, src, n, x, y, z, f);
-    pull_all<S, I + 1>(p, src, n, x, y, z, f);
-  }
+// Source column of a shifted direction: x - c_x with periodic wrap, the
+// inflow column (x = -1: returns -1), or the outflow copy (clamped).
+__device__ __forceinline__ int source_x(const StepParams& p, int x, int dx) {
+  int xs = x - dx;
+  if (xs < 0) xs = p.x_io ? -1 : p.nx - 1;
+  if (xs >= p.nx) xs = p.x_io ? p.nx - 1 : 0;
+  return xs;
 }
 
-// Moments, canopy-corrected velocity and total force density.
 struct Macro {
   float drho, rho, ux, uy, uz, Fx, Fy, Fz;
 };
 
+// Directions come in pairs (i, i+1) with c_{i+1} = -c_i (i odd).  Pair sums
+// and differences give the moments with half the additions.
 __device__ __forceinline__ Macro moments(const float* f, float gx, float gy, float gz, float k) {
   Macro m;
-  float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+  float sm[NQ], df[NQ];
 #pragma unroll
-  for (int i = 0; i < NQ; i++) {
-    drho += f[i];
-    if (cx(i) == 1) mx += f[i];
-    if (cx(i) == -1) mx -= f[i];
-    if (cy(i) == 1) my += f[i];
-    if (cy(i) == -1) my -= f[i];
-    if (cz(i) == 1) mz += f[i];
-    if (cz(i) == -1) mz -= f[i];
+  for (int i = 1; i < NQ; i += 2) {
+    sm[i] = f[i] + f[i + 1];
+    df[i] = f[i] - f[i + 1];
+  }
+  float drho = f[0];
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) drho += sm[i];
+  float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    if (cx(i) == 1) mx += df[i];
+    if (cx(i) == -1) mx -= df[i];
+    if (cy(i) == 1) my += df[i];
+    if (cy(i) == -1) my -= df[i];
+    if (cz(i) == 1) mz += df[i];
+    if (cz(i) == -1) mz -= df[i];
   }
   const float rho = 1.0f + drho;
   const float inv_rho = 1.0f / rho;
@@ -232,43 +226,72 @@ __device__ __forceinline__ Macro moments(const float* f, float gx, float gy, flo
   return m;
 }
 
-// BGK-Smagorinsky collision with Guo forcing, in place on shifted populations.
-// The equilibrium is evaluated twice (for Pi_neq, then for the relaxation)
-// instead of being kept in 19 more registers.
-__device__ __forceinline__ float feq_shifted(int i, const Macro& m, float uu) {
-  const float cu = cx(i) * m.ux + cy(i) * m.uy + cz(i) * m.uz;
-  // f_eq - w_i (Eq. local_eq with rho = 1 + drho)
-  return wgt(i) * (m.drho + m.rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-}
-
-__device__ __forceinline__ void collide(float* f, const Macro& m, float tau0, float c18) {
+// BGK-Smagorinsky collision with Guo forcing on shifted populations, written
+// per pair (i, i+1): with e = c_i . u and h = c_i . F,
+//   f_eq - w = W (drho + rho (4.5 e^2 - 1.5 u.u)) +- 3 W rho e      (Eq. local_eq)
+//   F_i      = (1 - om/2) W (9 e h - 3 u.F)      +- 3 (1 - om/2) W h (Eq. bodyforce)
+// so the even and odd parts are evaluated once per pair.  Pi_neq (Eq. tensor)
+// needs only the pair sums of f - f_eq.  The post-collision values
+// f* = f - om (f - f_eq) + F_i are handed to `emit(i, value)`.
+template <class Emit>
+__device__ __forceinline__ void collide(const float* f, const Macro& m, float tau0, float c18,
+                                        Emit&& emit) {
   const float ux = m.ux, uy = m.uy, uz = m.uz;
   const float uu = ux * ux + uy * uy + uz * uz;
+  const float base = m.drho - 1.5f * m.rho * uu;  // even part without the e^2 term
+  const float r45 = 4.5f * m.rho;
+  const float r3 = 3.0f * m.rho;
+  float sym[NQ];
   float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
-  for (int i = 0; i < NQ; i++) {
-    const float d = f[i] - feq_shifted(i, m, uu);
-    if (cx(i) != 0) pxx += d;
-    if (cy(i) != 0) pyy += d;
-    if (cz(i) != 0) pzz += d;
-    if (cx(i) * cy(i) == 1) pxy += d;
-    if (cx(i) * cy(i) == -1) pxy -= d;
-    if (cx(i) * cz(i) == 1) pxz += d;
-    if (cx(i) * cz(i) == -1) pxz -= d;
-    if (cy(i) * cz(i) == 1) pyz += d;
-    if (cy(i) * cz(i) == -1) pyz -= d;
+  for (int i = 1; i < NQ; i += 2) {
+    const float w = wgt(i);
+    float ei;
+    if (i == 1) ei = ux; else if (i == 3) ei = uy; else if (i == 5) ei = uz;
+    else if (i == 7) ei = ux + uy; else if (i == 9) ei = ux - uy;
+    else if (i == 11) ei = ux + uz; else if (i == 13) ei = ux - uz;
+    else if (i == 15) ei = uy + uz; else ei = uy - uz;
+    sym[i] = w * (base + r45 * ei * ei);
+    const float npair = (f[i] + f[i + 1]) - 2.0f * sym[i];  // sum over the pair of f - f_eq
+    if (cx(i) != 0) pxx += npair;
+    if (cy(i) != 0) pyy += npair;
+    if (cz(i) != 0) pzz += npair;
+    if (cx(i) * cy(i) == 1) pxy += npair;
+    if (cx(i) * cy(i) == -1) pxy -= npair;
+    if (cx(i) * cz(i) == 1) pxz += npair;
+    if (cx(i) * cz(i) == -1) pxz -= npair;
+    if (cy(i) * cz(i) == 1) pyz += npair;
+    if (cy(i) * cz(i) == -1) pyz -= npair;
   }
   const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
   const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * sqrtf(q2) / m.rho));
   const float om = 1.0f / tau;
+  const float keep = 1.0f - om;
   const float pre = 1.0f - 0.5f * om;
-  const float uF = ux * m.Fx + uy * m.Fy + uz * m.Fz;
+  const float uF3 = 3.0f * (ux * m.Fx + uy * m.Fy + uz * m.Fz);
+  // rest population: e = h = 0
+  {
+    const float w = wgt(0);
+    const float feq0 = w * base;
+    emit(0, keep * f[0] + om * feq0 - pre * w * uF3);
+  }
 #pragma unroll
-  for (int i = 0; i < NQ; i++) {
-    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-    const float cF = cx(i) * m.Fx + cy(i) * m.Fy + cz(i) * m.Fz;
-    const float Fi = pre * wgt(i) * (3.0f * (cF - uF) + 9.0f * cu * cF);
-    f[i] = f[i] - om * (f[i] - feq_shifted(i, m, uu)) + Fi;
+  for (int i = 1; i < NQ; i += 2) {
+    const float w = wgt(i);
+    float ei, hi;
+    if (i == 1) { ei = ux; hi = m.Fx; } else if (i == 3) { ei = uy; hi = m.Fy; }
+    else if (i == 5) { ei = uz; hi = m.Fz; }
+    else if (i == 7) { ei = ux + uy; hi = m.Fx + m.Fy; }
+    else if (i == 9) { ei = ux - uy; hi = m.Fx - m.Fy; }
+    else if (i == 11) { ei = ux + uz; hi = m.Fx + m.Fz; }
+    else if (i == 13) { ei = ux - uz; hi = m.Fx - m.Fz; }
+    else if (i == 15) { ei = uy + uz; hi = m.Fy + m.Fz; }
+    else { ei = uy - uz; hi = m.Fy - m.Fz; }
+    const float pw = pre * w;
+    const float even = om * sym[i] + pw * (9.0f * ei * hi - uF3);
+    const float odd = om * (w * r3 * ei) + 3.0f * pw * hi;
+    emit(i, keep * f[i] + (even + odd));
+    emit(i + 1, keep * f[i + 1] + (even - odd));
   }
 }
 
@@ -300,116 +323,380 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// ---- the fused step -----------------------------------------------------------------
-template <int S, bool STATS>
-__global__ void __launch_bounds__(256) step_kernel(StepParams p) {
-  using T = typename Store<S>::T;
-  const T* __restrict__ src = static_cast<const T*>(p.src);
-  T* __restrict__ dst = static_cast<T*>(p.dst);
-
-  __shared__ float s_stats[9 * MAX_XBINS];
-  __shared__ float s_ub[32];
-  __shared__ float s_gx;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nthreads = blockDim.x * blockDim.y;
-  const int lane = tid & 31, warp = tid >> 5;
-  if (STATS) {
-    for (int k = tid; k < 9 * p.nbins; k += nthreads) s_stats[k] = 0.f;
+// Plane statistics: reduce the per-thread sums (warp, then shared memory) and
+// add them to the FP64 accumulators of row y.  Called by every thread.
+__device__ __forceinline__ void flush_plane_stats(const StepParams& p, float* q, int& last_x,
+                                                  int y, float* s_stats, int lane, int tid,
+                                                  int nthreads) {
+  // warp-level reduction when the warp shares one x-bin, else per lane
+  const int bin = last_x >= 0 ? (int)(((long long)last_x * p.nbins) / p.nx) : -1;
+  const unsigned act = __ballot_sync(0xffffffffu, bin >= 0);
+  if (act) {
+    const int b0 = __shfl_sync(0xffffffffu, bin, __ffs(act) - 1);
+    const int key = bin >= 0 ? bin : b0;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    if (same == 0xffffffffu) {
+#pragma unroll
+      for (int kk = 0; kk < 9; kk++) {
+        const float v = warp_sum(q[kk]);
+        if (lane == 0) atomicAdd(&s_stats[kk * p.nbins + key], v);
+      }
+    } else if (bin >= 0) {
+#pragma unroll
+      for (int kk = 0; kk < 9; kk++) atomicAdd(&s_stats[kk * p.nbins + bin], q[kk]);
+    }
   }
-  if (warp == 0) {
-    const float v = controlled_gx(p, lane);
-    if (lane == 0) s_gx = v;
+#pragma unroll
+  for (int kk = 0; kk < 9; kk++) q[kk] = 0.f;
+  last_x = -1;
+  __syncthreads();
+  for (int kk = tid; kk < 9 * p.nbins; kk += nthreads) {
+    const float v = s_stats[kk];
+    if (v != 0.f) {
+      const int qk = kk / p.nbins, b = kk - qk * p.nbins;
+      atomicAdd(&p.stats[((long long)qk * p.nbins + b) * p.ny + y], (double)v);
+    }
+    s_stats[kk] = 0.f;
   }
   __syncthreads();
-  const float gx = s_gx, gy = p.g[1], gz = p.g[2];
+}
 
-  const long long t0 = (long long)blockIdx.x * p.ntiles / gridDim.x;
-  const long long t1 = (long long)(blockIdx.x + 1) * p.ntiles / gridDim.x;
-  // tile t -> (y, z-group, x-chunk), walked incrementally
-  int xc = (int)(t0 % p.nxc);
-  long long rest = t0 / p.nxc;
-  int zg = (int)(rest % p.nzg);
-  int y = (int)(rest / p.nzg);
-
-  float ub_acc = 0.f;
-  bool bad = false;
-
-  for (long long t = t0; t < t1; t++) {
-    const int x = xc * blockDim.x + threadIdx.x;
-    const int z = zg * blockDim.y + threadIdx.y;
-    const bool active = (x < p.nx) && (z < p.nz);
-    float q[9];
-    int bin = 0;
-    if (active) {
-      const Nbr n = neighbours(p, x, y, z);
-      float f[NQ];
-      pull_all<S>(p, src, n, x, y, z, f);
-      const Macro m = moments(f, gx, gy, gz, drag_factor(p, x, y));
-      collide(f, m, p.tau0, p.c18);
-      const long long own = (long long)((y * p.nz + z) * p.pitch + x);
-#pragma unroll
-      for (int i = 0; i < NQ; i++) Store<S>::st(dst + p.qoff[i] + own, f[i]);
-      ub_acc += m.ux;
-      bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
-      if (STATS) {
-        q[0] = m.ux; q[1] = m.uy; q[2] = m.uz;
-        q[3] = m.ux * m.ux; q[4] = m.uy * m.uy; q[5] = m.uz * m.uz;
-        q[6] = m.ux * m.uy; q[7] = m.ux * m.uz; q[8] = m.uy * m.uz;
-        bin = (int)(((long long)x * p.nbins) / p.nx);
-      }
-    } else if (STATS) {
-#pragma unroll
-      for (int k = 0; k < 9; k++) q[k] = 0.f;
-      bin = -1;
-    }
-    if (STATS) {
-      // warp-level reduction when the warp shares one x-bin, else per lane
-      const unsigned act = __ballot_sync(0xffffffffu, bin >= 0);
-      if (act) {
-        const int b0 = __shfl_sync(0xffffffffu, bin, __ffs(act) - 1);
-        const int key = bin >= 0 ? bin : b0;
-        const unsigned same = __match_any_sync(0xffffffffu, key);
-        if (same == 0xffffffffu) {
-#pragma unroll
-          for (int k = 0; k < 9; k++) {
-            const float v = warp_sum(q[k]);
-            if (lane == 0) atomicAdd(&s_stats[k * p.nbins + key], v);
-          }
-        } else if (bin >= 0) {
-#pragma unroll
-          for (int k = 0; k < 9; k++) atomicAdd(&s_stats[k * p.nbins + bin], q[k]);
-        }
-      }
-    }
-    // advance to the next tile; flush the plane statistics when y changes
-    const int y_now = y;
-    if (++xc == p.nxc) {
-      xc = 0;
-      if (++zg == p.nzg) { zg = 0; ++y; }
-    }
-    if (STATS && (y != y_now || t + 1 == t1)) {
-      __syncthreads();
-      for (int k = tid; k < 9 * p.nbins; k += nthreads) {
-        const float v = s_stats[k];
-        if (v != 0.f) {
-          const int qk = k / p.nbins, b = k - qk * p.nbins;
-          atomicAdd(&p.stats[((long long)qk * p.nbins + b) * p.ny + y_now], (double)v);
-        }
-        s_stats[k] = 0.f;
-      }
-      __syncthreads();
-    }
-  }
-
+// Step epilogue: health flags and this block's share of the bulk velocity.
+__device__ __forceinline__ void finish_step(const StepParams& p, float ub_acc, bool bad, bool late,
+                                            float* s_ub, int lane, int warp, int tid,
+                                            int nthreads) {
   if (bad) atomicOr(&p.state->nan_flag, 1u);
-  // bulk velocity of this step (read by the controller of the next step)
+  if (late) atomicOr(&p.state->timeout_flag, 1u);
   const float w = warp_sum(ub_acc);
   if (lane == 0) s_ub[warp] = w;
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
-    for (int k = 0; k < (nthreads + 31) / 32; k++) s += (double)s_ub[k];
+    for (int kk = 0; kk < (nthreads + 31) / 32; kk++) s += (double)s_ub[kk];
     p.ub_part[(long long)p.slot_write * MAX_BLOCKS + blockIdx.x] = s;
+  }
+}
+
+struct TileGeom {
+  int xc, zg, y;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const StepParams& p, long long t) {
+  TileGeom g;
+  g.xc = (int)(t % p.nxc);
+  const long long r = t / p.nxc;
+  g.zg = (int)(r % p.nzg);
+  g.y = (int)(r / p.nzg);
+  return g;
+}
+
+// ---- TMA bulk copies and mbarriers --------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+// bulk copy global -> shared: 16-byte aligned addresses, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// bounded wait for the phase with the given parity; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t k = 0; k < limit; k++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls (each may suspend ~us) before giving up
+
+// Direction components packed two bits each (1: +1, 2: -1) and the y-mirror
+// five bits each, so lanes holding different directions run the same code.
+__host__ __device__ constexpr uint64_t pack_comp(int axis) {
+  uint64_t w = 0;
+  for (int i = 0; i < NQ; i++) {
+    const int c = axis == 0 ? cx(i) : axis == 1 ? cy(i) : cz(i);
+    w |= (uint64_t)(c == 1 ? 1 : c == -1 ? 2 : 0) << (2 * i);
+  }
+  return w;
+}
+__host__ __device__ constexpr uint64_t pack_miry(int half) {
+  uint64_t w = 0;
+  for (int i = 0; i < NQ; i++) {
+    const int bit = 5 * i - 64 * half;
+    if (bit >= 0 && bit < 64) w |= (uint64_t)miry(i) << bit;
+    if (half == 1 && bit < 0 && bit > -5) w |= (uint64_t)miry(i) >> (-bit);
+  }
+  return w;
+}
+__device__ __forceinline__ int unpack_comp(uint64_t w, int i) {
+  const int b = (int)((w >> (2 * i)) & 3u);
+  return b == 1 ? 1 : (b == 2 ? -1 : 0);
+}
+__device__ __forceinline__ int unpack_miry(int i) {
+  constexpr uint64_t lo = pack_miry(0), hi = pack_miry(1);
+  const int bit = 5 * i;
+  const uint64_t v = bit < 64 ? ((lo >> bit) | (bit > 59 ? hi << (64 - bit) : 0)) : (hi >> (bit - 64));
+  return (int)(v & 31u);
+}
+
+// Shared-memory row of one direction: [halo | XT cells | halo], the halos
+// 16 bytes wide; cell tx sits at H + tx.
+template <int XT, int S>
+struct Stage {
+  using T = typename Store<S>::T;
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int SROW = XT + 2 * H;
+};
+
+// Producer: the lanes of one warp issue the bulk copies of tile t into a
+// stage: per tile row and direction, the chunk's cells of the source row plus
+// the ghost slot on the side its c_x streams from (16 bytes on that side).
+template <int XT, int S>
+__device__ __noinline__ void issue_tile(const StepParams& p, long long t, unsigned char* stage,
+                                        uint64_t* bar, int lane) {
+  using T = typename Store<S>::T;
+  using Gm = Geo<XT, S>;
+  using St = Stage<XT, S>;
+  constexpr int H = St::H;
+  constexpr uint64_t kCX = pack_comp(0), kCY = pack_comp(1), kCZ = pack_comp(2);
+  const TileGeom g = tile_geom(p, t);
+  const int ry = blockDim.y;
+  const int nrows = min(ry, p.nz - g.zg * ry);
+  const int n = min(XT, p.nx - g.xc * XT);
+  const int nal = (n + H - 1) / H * H;  // cells rounded up to 16 bytes (stays in the row)
+  const bool eq_top_row = p.y_walls && p.top == 3 && g.y == p.ny - 1;
+  // bytes per tile row: 19 rows of nal cells, the 10 with c_x != 0 with their
+  // 16-byte ghost block (also for bounce-back rows, where it is not read);
+  // constant rows (equilibrium top) are not copied
+  uint32_t per_row = 0;
+  for (int i = 0; i < NQ; i++) {
+    if (eq_top_row && cy(i) == -1) continue;
+    per_row += (uint32_t)(nal + (cx(i) != 0 ? H : 0)) * sizeof(T);
+  }
+  if (lane == 0) mbar_expect_tx(bar, per_row * (uint32_t)nrows);
+  __syncwarp();
+  const T* base = static_cast<const T*>(p.src) + Gm::G;
+  for (int k = lane; k < nrows * NQ; k += 32) {
+    const int r = k / NQ, i = k - r * NQ;
+    const int z = g.zg * ry + r;
+    int q, ys, zs;
+    const int kind = row_source(p, i, unpack_comp(kCY, i), unpack_comp(kCZ, i), g.y, z, q, ys, zs);
+    if (kind == SRC_CONST) continue;
+    const int dxi = unpack_comp(kCX, i);
+    const T* src = base + (long long)((ys * p.nz + zs) * p.nxc + g.xc) * Gm::ROW + (long long)q * Gm::XTP;
+    T* dst = reinterpret_cast<T*>(stage) + (r * NQ + i) * St::SROW + H;
+    const int lo = dxi == 1 ? -H : 0, len = nal + (dxi != 0 ? H : 0);
+    bulk_g2s(dst + lo, src + lo, (uint32_t)len * sizeof(T), bar);
+  }
+}
+
+// ---- the fused step -----------------------------------------------------------------
+// Persistent blocks walk a contiguous range of tiles (tile = ry rows of XT
+// cells at one y).  One warp keeps `nstage` tiles of source rows in flight
+// (TMA bulk copies into shared memory, one mbarrier per stage); every thread
+// reads its cell's 19 populations from the staged rows (shared loads at
+// immediate offsets), collides in registers (moments, canopy velocity,
+// Smagorinsky tau, BGK + Guo) and stores whole lines to HBM.  A stage is
+// released when its last warp has consumed it (monotonic ticket); that warp
+// issues the refill, so no block-wide barrier sits in the loop.
+template <int XT, int S, bool STATS>
+__global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
+  using T = typename Store<S>::T;
+  using Gm = Geo<XT, S>;
+  using St = Stage<XT, S>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ float s_stats[9 * MAX_XBINS];
+  __shared__ float s_ub[32];
+  __shared__ float s_gx;
+  __shared__ __align__(8) uint64_t s_bar[8];
+  __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
+
+  const int tx = threadIdx.x;
+  const int tid = threadIdx.y * XT + tx;
+  const int nthreads = XT * blockDim.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  const unsigned int nwarps = (unsigned int)nthreads / 32;
+  const int stage_bytes = (int)blockDim.y * NQ * St::SROW * (int)sizeof(T);
+
+  const long long t0l = (long long)blockIdx.x * p.ntiles / gridDim.x;
+  const int ntile = (int)((long long)(blockIdx.x + 1) * p.ntiles / gridDim.x - t0l);
+
+  if (tid == 0) {
+    for (int k = 0; k < p.nstage; k++) {
+      mbar_init(&s_bar[k], 1);
+      s_done[k] = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (STATS) {
+    for (int k = tid; k < 9 * p.nbins; k += nthreads) s_stats[k] = 0.f;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < p.nstage && k < ntile; k++)
+      issue_tile<XT, S>(p, t0l + k, smem + k * stage_bytes, &s_bar[k], lane);
+    const float v = controlled_gx(p, lane);
+    if (lane == 0) s_gx = v;
+  }
+  __syncthreads();
+  const float gx = s_gx, gy = p.g[1], gz = p.g[2];
+  T* dst = static_cast<T*>(p.dst) + Gm::G + tx;
+  T* const dst0 = static_cast<T*>(p.dst) + Gm::G;  // slot G of direction 0, chunk-row 0
+
+  TileGeom g = tile_geom(p, t0l);
+  float ub_acc = 0.f;
+  bool bad = false, late = false;
+  float q[9];
+#pragma unroll
+  for (int k = 0; k < 9; k++) q[k] = 0.f;
+  int last_x = -1;  // column of the last cell this thread accumulated (-1: none)
+  // with one x-chunk per row a thread keeps its column, so its x-bin is fixed
+  const bool flush_each_tile = p.nbins > 1 && p.nxc > 1;
+
+  for (int t = 0; t < ntile; t++) {
+    const int st = t % p.nstage;
+    const uint32_t parity = (uint32_t)((t / p.nstage) & 1);
+    const unsigned char* stage = smem + st * stage_bytes;
+    const int x0 = g.xc * XT;
+    const int x = x0 + tx;
+    const int z = g.zg * blockDim.y + threadIdx.y;
+    const int y = g.y;
+    const bool active = (x < p.nx) && (z < p.nz);
+
+    const bool ready = mbar_wait(&s_bar[st], parity, WAIT_LIMIT);
+    if (!ready) late = true;
+    float f[NQ];
+    Macro m;
+    if (active && ready) {
+      const T* sm = reinterpret_cast<const T*>(stage) + threadIdx.y * NQ * St::SROW + St::H + tx;
+      // streaming from the staged rows; at a free-slip top the staged row is
+      // already the mirrored one, so only bounce-back (own column) and the
+      // equilibrium top (constant) differ, on the five directions entering
+      // through the wall
+#pragma unroll
+      for (int i = 0; i < NQ; i++) f[i] = Store<S>::to_float(sm[i * St::SROW - cx(i)]);
+      if (p.y_walls) {
+        if (y == 0) {
+#pragma unroll
+          for (int i = 0; i < NQ; i++)
+            if (cy(i) == 1) f[i] = Store<S>::to_float(sm[i * St::SROW]);
+        }
+        if (y == p.ny - 1 && p.top != 2) {
+#pragma unroll
+          for (int i = 0; i < NQ; i++)
+            if (cy(i) == -1) f[i] = p.top == 1 ? Store<S>::to_float(sm[i * St::SROW]) : p.feq_top[i];
+        }
+      }
+      m = moments(f, gx, gy, gz, drag_factor(p, x, y));
+    }
+    // release the stage: the moments consumed every staged value of this warp
+    __syncwarp();
+    unsigned int ticket = 0;
+    if (lane == 0) ticket = atomicAdd(&s_done[st], 1u);
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket % nwarps == nwarps - 1 && t + p.nstage < ntile) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_tile<XT, S>(p, t0l + t + p.nstage, smem + st * stage_bytes, &s_bar[st], lane);
+    }
+    if (active && ready) {
+      const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
+      T* out = dst + (long long)(unsigned)(crow0 + g.xc) * Gm::ROW;
+      // ghost slots this cell feeds (edge lanes only): its c_x = +1 values to
+      // the left ghost of the chunk on its right, its c_x = -1 values to the
+      // right ghost of the chunk on its left (periodic wrap), or beside itself
+      // at an outflow (zero gradient)
+      T* gr = nullptr;
+      T* gl = nullptr;
+      if (tx == 0 || tx == XT - 1 || x == p.nx - 1) {
+        if (x == p.nx - 1) {
+          if (!p.x_io) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
+          else gl = out + 1;
+        } else if (tx == XT - 1) {
+          gr = dst0 + (long long)(unsigned)(crow0 + g.xc + 1) * Gm::ROW - 1;
+        }
+        if (x == 0) {
+          if (!p.x_io) {
+            const int xl = p.nxc - 1;
+            gl = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
+          }
+        } else if (tx == 0) {
+          gl = dst0 + (long long)(unsigned)(crow0 + g.xc - 1) * Gm::ROW + XT;
+        }
+      }
+      collide(f, m, p.tau0, p.c18, [&](int i, float v) {
+        Store<S>::st(out + i * Gm::XTP, v);
+        if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
+        if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
+      });
+      ub_acc += m.ux;
+      bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
+      if (STATS) {
+        q[0] += m.ux; q[1] += m.uy; q[2] += m.uz;
+        q[3] += m.ux * m.ux; q[4] += m.uy * m.uy; q[5] += m.uz * m.uz;
+        q[6] += m.ux * m.uy; q[7] += m.ux * m.uz; q[8] += m.uy * m.uz;
+        last_x = x;
+      }
+    }
+    // advance to the next tile; flush the plane statistics when y changes
+    const int y_now = g.y;
+    if (++g.xc == p.nxc) {
+      g.xc = 0;
+      if (++g.zg == p.nzg) { g.zg = 0; ++g.y; }
+    }
+    if (STATS && (g.y != y_now || t + 1 == ntile || flush_each_tile))
+      flush_plane_stats(p, q, last_x, y_now, s_stats, lane, tid, nthreads);
+  }
+  finish_step(p, ub_acc, bad, late, s_ub, lane, warp, tid, nthreads);
+}
+
+// ---- ghost slots from the cells (after init, set_f) ----------------------------------
+// One thread per (chunk-row, side, direction with c_x != 0).  The inflow
+// ghosts hold the inflow equilibrium and are never rewritten by a step.
+template <int XT, int S>
+__global__ void ghost_kernel(StepParams p, void* fv) {
+  using T = typename Store<S>::T;
+  using Gm = Geo<XT, S>;
+  T* f = static_cast<T*>(fv) + Gm::G;
+  const long long rows = (long long)p.ny * p.nz * p.nxc;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < rows * 10;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long cr = k / 10;
+    const int j = (int)(k - cr * 10);
+    const int xc = (int)(cr % p.nxc);
+    const long long yz = cr / p.nxc;
+    const int y = (int)(yz / p.nz);
+    const int x0 = xc * XT, n = min(XT, p.nx - x0);
+    // j < 5: left ghost of c_x = +1 directions 1 7 9 11 13; j >= 5: right, 2 8 10 12 14
+    const int i = j < 5 ? (j == 0 ? 1 : 5 + 2 * j) : (j == 5 ? 2 : 2 * (j - 5) + 6);
+    T* row = f + cr * Gm::ROW + (long long)i * Gm::XTP;
+    auto cell = [&](int xc2, int t) { return f[((yz * p.nxc) + xc2) * Gm::ROW + (long long)i * Gm::XTP + t]; };
+    if (j < 5) {
+      if (xc > 0) row[-1] = cell(xc - 1, XT - 1);
+      else if (p.x_io) row[-1] = Store<S>::from_double((double)p.feq_in[y * NQ + i]);
+      else row[-1] = cell(p.nxc - 1, p.nx - 1 - (p.nxc - 1) * XT);
+    } else {
+      if (xc < p.nxc - 1) row[n] = cell(xc + 1, 0);
+      else if (p.x_io) row[n] = row[n - 1];
+      else row[n] = cell(0, 0);
+    }
   }
 }
 
@@ -428,16 +715,16 @@ __host__ __device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t n
 
 struct InitParams {
   void* f;
-  int nx, ny, nz, pitch;
-  long long plane;
+  int nx, ny, nz, nxc;
   const double* u_prof;  // ny values or nullptr
   uint64_t seed;
   double amp;
 };
 
-template <int S>
+template <int XT, int S>
 __global__ void init_kernel(InitParams p) {
   using T = typename Store<S>::T;
+  using Gm = Geo<XT, S>;
   T* f = static_cast<T*>(p.f);
   const long long n = (long long)p.nx * p.ny * p.nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
@@ -449,30 +736,31 @@ __global__ void init_kernel(InitParams p) {
     double u[3] = {p.u_prof ? p.u_prof[y] : 0.0, 0.0, 0.0};
     for (int a = 0; a < 3; a++) u[a] += p.amp * uniform_pm1(p.seed, 3ull * (uint64_t)c + a);
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const long long own = (long long)((y * p.nz + z) * p.pitch + x);
+    T* cell = f + (((long long)y * p.nz + z) * p.nxc + x / XT) * Gm::ROW + Gm::G + x % XT;
 #pragma unroll
     for (int i = 0; i < NQ; i++) {
       const double cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
       const double fs = wgt_d(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);  // f_eq(1,u) - w_i
-      f[(long long)i * p.plane + own] = Store<S>::from_double(fs);
+      cell[i * Gm::XTP] = Store<S>::from_double(fs);
     }
   }
 }
 
 // ---- global mass: deterministic two-pass FP64 reduction ------------------------------
-template <int S>
-__global__ void mass_partial_kernel(const void* fv, int nx, int pitch, long long rows, long long plane,
-                                    double* partial) {
+template <int XT, int S>
+__global__ void mass_partial_kernel(const void* fv, int nx, long long rows, int nxc, double* partial) {
   using T = typename Store<S>::T;
+  using Gm = Geo<XT, S>;
   const T* f = static_cast<const T*>(fv);
   double acc = 0.0;
-  const long long per_plane = rows * nx;
-  const long long total = per_plane * NQ;
+  const long long total = rows * nx * NQ;  // (row, q, x) over the real cells
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
-    const long long q = k / per_plane, rem = k - q * per_plane;
-    const long long row = rem / nx, x = rem - row * nx;
-    acc += (double)Store<S>::ld(f + q * plane + row * pitch + x);
+    const long long row = k / ((long long)nx * NQ);
+    const long long rem = k - row * nx * NQ;
+    const int q = (int)(rem / nx), x = (int)(rem - (long long)q * nx);
+    acc += (double)Store<S>::ld(f + (row * nxc + x / XT) * Gm::ROW + (long long)q * Gm::XTP + Gm::G +
+                                x % XT);
   }
   __shared__ double s[256];
   s[threadIdx.x] = acc;
@@ -493,21 +781,33 @@ __global__ void mass_final_kernel(const double* partial, int n, double base, dou
 }
 
 // ---- macroscopic fields of the next step (pull + moments only) ------------------------
-template <int S>
+// Direct loads with the same boundary rules as the step (not performance critical).
+template <int XT, int S>
 __global__ void macro_kernel(StepParams p, float* out) {
   using T = typename Store<S>::T;
-  const T* src = static_cast<const T*>(p.src);
   const long long n = (long long)p.nx * p.ny * p.nz;
   const float gx = controlled_gx(p, threadIdx.x & 31);  // blockDim.x is a multiple of 32
+  const T* src = static_cast<const T*>(p.src);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(c % p.nx);
     const long long r = c / p.nx;
     const int y = (int)(r % p.ny);
     const int z = (int)(r / p.ny);
-    const Nbr nb = neighbours(p, x, y, z);
     float f[NQ];
-    pull_all<S>(p, src, nb, x, y, z, f);
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+      int q, ys, zs;
+      const int kind = row_source(p, i, cy(i), cz(i), y, z, q, ys, zs);
+      if (kind == SRC_CONST) {
+        f[i] = p.feq_top[i];
+      } else if (kind == SRC_OWN_X) {
+        f[i] = Store<S>::ld(src + pop_index<XT, S>(p, q, x, ys, zs));
+      } else {
+        const int xs = source_x(p, x, cx(i));
+        f[i] = xs < 0 ? p.feq_in[ys * NQ + q] : Store<S>::ld(src + pop_index<XT, S>(p, q, xs, ys, zs));
+      }
+    }
     const Macro m = moments(f, gx, p.g[1], p.g[2], drag_factor(p, x, y));
     out[c] = m.rho;
     out[n + c] = m.ux;
