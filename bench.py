@@ -45,7 +45,38 @@ def parse():
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16 storage legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", metavar="NXxNYxNZ", default=None,
+                    help="run a few steps of the channel workload at this size and exit "
+                         "(the case the ncu summaries under profiles/ capture)")
     return ap.parse_args()
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources, to tell whether profiles/ counters still apply."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2206_15454_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(storage_name, cells):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled from the captured case to `cells`; None if the kernel changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    e = t.get("storage", {}).get(storage_name)
+    if not e:
+        return None
+    return (e["dram_read_bytes"] + e["dram_write_bytes"]) * cells / e["cells"]
 
 
 def peaks():
@@ -239,8 +270,10 @@ def run_ours(args):
                    "bytes_per_lup": bpl, "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": f"{ws} independent replica(s)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "frac": round(achieved / hbm, 4),
+                     "traffic": measured_traffic(args.storage, cells),
                      "kernel": "step_kernel", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bpl * cells,
                      "launch_ms": launch_ms},
         "gpu_launches": args.steps,
         "clocks": clk,
@@ -274,7 +307,8 @@ def run_ours(args):
             res[name] = {"value": round(cells * args.steps * ws / (tot * 1e-3) / 1e6, 1),
                          "unit": "MLUPS", "ms_per_step": tot / args.steps,
                          "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
-                                      "unit": "GB/s", "frac": round(ach / hbm, 4)},
+                                      "unit": "GB/s", "frac": round(ach / hbm, 4),
+                                      "traffic": measured_traffic(name, cells)},
                          "rel_l2_f_vs_f32_after_100_steps": err}
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(W.channel_les, args.cpu_seconds)
@@ -328,9 +362,28 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile_case(args):
+    """A few steps of the channel workload at a chosen size (ncu capture target)."""
+    import torch
+
+    import paper_2206_15454_b300 as P
+    import workloads as W
+
+    nx, ny, nz = (int(v) for v in args.profile.lower().split("x"))
+    torch.cuda.set_device(0)
+    d = P.Domain(W.channel_les(nx, ny, nz), P.STORAGE_NAMES[args.storage])
+    d.stats_reset(True)
+    d.step(6)
+    d.sync()
+    d.close()
+    print(f"profile case {nx}x{ny}x{nz} {args.storage}: 6 steps done")
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
