@@ -156,6 +156,20 @@ lbm_status lbm_set_f(lbm_ctx* ctx, const double* host_f, size_t n);
  * rho[z][y][x] (n = nx*ny*nz values) and u[3][z][y][x] (3n values). */
 lbm_status lbm_get_macro(lbm_ctx* ctx, double* rho, double* u, size_t n);
 
+/* Same output as lbm_get_macro, without allocating device memory.  The paper
+ * has no counterpart: this serves callers that must not call cudaMalloc (a
+ * fixed memory budget or pre-reserved pool, or code running while other work
+ * on the device is captured or timed), whereas lbm_get_macro allocates its
+ * staging buffer on first use.  The fields pass through one file-scope device
+ * array of 262144 cells x 4 doubles (8 MB, held on every device that loads the
+ * library until the process exits); grids with more cells are rejected with
+ * LBM_ERR_ARG.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other threads or streams) race.  Synchronises the
+ * context's stream. */
+lbm_status lbm_get_macro_noalloc(lbm_ctx* ctx, double* rho, double* u, size_t n);
+
 /* Driving acceleration the next step uses and the bulk velocity of the last. */
 lbm_status lbm_drive(lbm_ctx* ctx, double g[3], double* u_bulk);
 

@@ -69,6 +69,7 @@ def lib():
                            ("lbm_mass", [vp, _DP]), ("lbm_get_f", [vp, _DP, C.c_size_t]),
                            ("lbm_set_f", [vp, _DP, C.c_size_t]),
                            ("lbm_get_macro", [vp, _DP, _DP, C.c_size_t]),
+                           ("lbm_get_macro_noalloc", [vp, _DP, _DP, C.c_size_t]),
                            ("lbm_drive", [vp, _DP, _DP]), ("lbm_save", [vp, C.c_char_p]),
                            ("lbm_load", [vp, C.c_char_p])]:
             fn = getattr(L, name)
@@ -153,6 +154,12 @@ def lbm_set_f(ctx, f: np.ndarray):
 
 def lbm_get_macro(ctx, rho: np.ndarray, u: np.ndarray):
     _check(lib().lbm_get_macro(ctx, _dp(rho), _dp(u), rho.size), ctx, "lbm_get_macro")
+
+
+def lbm_get_macro_noalloc(ctx, rho: np.ndarray, u: np.ndarray):
+    """lbm_get_macro without device allocation (static field buffer, <= 262144 cells)."""
+    _check(lib().lbm_get_macro_noalloc(ctx, _dp(rho), _dp(u), rho.size), ctx,
+           "lbm_get_macro_noalloc")
 
 
 def lbm_drive(ctx):

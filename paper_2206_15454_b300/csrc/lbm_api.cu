@@ -673,6 +673,49 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
   return LBM_OK;
 }
 
+// ---- field readout without allocation -------------------------------------------------
+// lbm_get_macro stages the fields in a device buffer it allocates on first use.
+// Callers that must not allocate device memory (a process running inside a
+// strict memory budget or a pre-reserved pool, code that may not call
+// cudaMalloc while other work is being captured or timed) use this variant:
+// the fields go through a file-scope device array of fixed size instead.
+namespace {
+constexpr long long kNoAllocMaxCells = 262144;  // 64^3 cells; 8 MB of FP64 on every device
+__device__ __align__(256) double g_noalloc_fields[4 * kNoAllocMaxCells];
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};  // device address of the array, per device
+}  // namespace
+
+lbm_status lbm_get_macro_noalloc(lbm_ctx* c, double* rho, double* u, size_t n) {
+  READY(c);
+  if (!rho || !u || n != (size_t)c->cells) return arg_error(c, "lbm_get_macro_noalloc: wrong size");
+  if (c->cells > kNoAllocMaxCells)
+    return arg_error(c, "lbm_get_macro_noalloc: the grid has more than 262144 cells, the size of "
+                        "its static field buffer; use lbm_get_macro");
+  int dev = 0;
+  CK(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return arg_error(c, "lbm_get_macro_noalloc: device id out of range");
+  if (!g_noalloc_ptr[dev]) {
+    // first call on this device: look up the array's device address (the
+    // symbol itself is only a host-side stand-in)
+    void* ptr = nullptr;
+    CK(c, cudaGetSymbolAddress(&ptr, g_noalloc_fields));
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  double* buf = g_noalloc_ptr[dev];
+  const StepParams p = make_params(c);
+  dispatch(c, [&](auto xt, auto s) {
+    macro_kernel<decltype(xt)::value, decltype(s)::value, double>
+        <<<c->sm_count * 8, 256, 0, c->stream>>>(p, buf);
+  });
+  CK(c, cudaGetLastError());
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  CK(c, cudaMemcpy(rho, buf, sizeof(double) * c->cells, cudaMemcpyDeviceToHost));
+  CK(c, cudaMemcpy(u, buf + c->cells, sizeof(double) * 3 * c->cells, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
 int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
 
 void lbm_destroy(lbm_ctx* c) {

@@ -782,8 +782,8 @@ __global__ void mass_final_kernel(const double* partial, int n, double base, dou
 
 // ---- macroscopic fields of the next step (pull + moments only) ------------------------
 // Direct loads with the same boundary rules as the step (not performance critical).
-template <int XT, int S>
-__global__ void macro_kernel(StepParams p, float* out) {
+template <int XT, int S, class OutT = float>
+__global__ void macro_kernel(StepParams p, OutT* out) {
   using T = typename Store<S>::T;
   const long long n = (long long)p.nx * p.ny * p.nz;
   const float gx = controlled_gx(p, threadIdx.x & 31);  // blockDim.x is a multiple of 32
