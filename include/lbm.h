@@ -22,9 +22,13 @@
  *   layout f[q][z][y][x] with x fastest, 19*nx*ny*nz values.  The state is
  *   the post-collision population set of the last completed step.
  *   On the device the populations are stored as offsets from the lattice
- *   weights, f_i - w_i, in FP32, FP16 or BF16 (lbm_storage), structure of
- *   arrays [q][y][z][x] with rows padded to a multiple of 64 elements; two
- *   population sets are kept (pull scheme, double buffered).
+ *   weights, f_i - w_i, in FP32, FP16 or BF16 (lbm_storage), as a
+ *   row-interleaved structure of arrays f[y][z][x-chunk][q][x]: x is cut into
+ *   chunks of 64, 128 or 256 cells and each direction row of a chunk starts on
+ *   a 128-byte line, with one ghost slot on each side holding the neighbouring
+ *   column (previous/next chunk, periodic wrap, inflow equilibrium or
+ *   outflow copy).  Two population sets are kept (pull scheme, double
+ *   buffered).
  *
  * Errors
  *   Every call returns an lbm_status and never aborts.  An error other than
