@@ -231,12 +231,13 @@ void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
 }
 
 // Shared-memory stages: as many tiles in flight as fit beside three blocks
-// per SM (at most 8, at least 2).
+// per SM and their static shared memory (about 12 KB with statistics): at
+// most 8, at least 2.
 template <int XT, int S>
 void plan_stages(lbm_ctx* c) {
   using St = Stage<XT, S>;
   const size_t stage = (size_t)c->block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
-  c->nstage = (int)std::max<size_t>(2, std::min<size_t>(8, (70 * 1024) / stage));
+  c->nstage = (int)std::max<size_t>(2, std::min<size_t>(8, (62 * 1024) / stage));
   c->stage_smem = c->nstage * stage;
   cudaFuncSetAttribute(step_kernel<XT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)c->stage_smem);

@@ -470,7 +470,7 @@ struct Stage {
 // stage: per tile row and direction, the chunk's cells of the source row plus
 // the ghost slot on the side its c_x streams from (16 bytes on that side).
 template <int XT, int S>
-__device__ __noinline__ void issue_tile(const StepParams& p, long long t, unsigned char* stage,
+__device__ __forceinline__ void issue_tile(const StepParams& p, long long t, unsigned char* stage,
                                         uint64_t* bar, int lane) {
   using T = typename Store<S>::T;
   using Gm = Geo<XT, S>;
@@ -510,13 +510,14 @@ __device__ __noinline__ void issue_tile(const StepParams& p, long long t, unsign
 
 // ---- the fused step -----------------------------------------------------------------
 // Persistent blocks walk a contiguous range of tiles (tile = ry rows of XT
-// cells at one y).  One warp keeps `nstage` tiles of source rows in flight
+// cells at one y).  The block keeps `nstage` tiles of source rows in flight
 // (TMA bulk copies into shared memory, one mbarrier per stage); every thread
 // reads its cell's 19 populations from the staged rows (shared loads at
 // immediate offsets), collides in registers (moments, canopy velocity,
 // Smagorinsky tau, BGK + Guo) and stores whole lines to HBM.  A stage is
 // released when its last warp has consumed it (monotonic ticket); that warp
-// issues the refill, so no block-wide barrier sits in the loop.
+// issues the refill at the end of its iteration, so no block-wide barrier
+// sits in the loop.
 template <int XT, int S, bool STATS>
 __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   using T = typename Store<S>::T;
@@ -524,6 +525,9 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   using St = Stage<XT, S>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ float s_stats[9 * MAX_XBINS];
+  // per-thread statistics sums, kept in shared memory rather than registers
+  // (the collision needs every register the three-blocks-per-SM budget allows)
+  __shared__ float s_q[STATS ? 9 * 256 : 1];
   __shared__ float s_ub[32];
   __shared__ float s_gx;
   __shared__ __align__(8) uint64_t s_bar[8];
@@ -548,6 +552,8 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   }
   if (STATS) {
     for (int k = tid; k < 9 * p.nbins; k += nthreads) s_stats[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; k++) s_q[k * 256 + tid] = 0.f;
   }
   __syncthreads();
   if (warp == 0) {
@@ -564,9 +570,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   TileGeom g = tile_geom(p, t0l);
   float ub_acc = 0.f;
   bool bad = false, late = false;
-  float q[9];
-#pragma unroll
-  for (int k = 0; k < 9; k++) q[k] = 0.f;
+  float* const qs = s_q + tid;  // this thread's 9 sums, stride 256
   int last_x = -1;  // column of the last cell this thread accumulated (-1: none)
   // with one x-chunk per row a thread keeps its column, so its x-bin is fixed
   const bool flush_each_tile = p.nbins > 1 && p.nxc > 1;
@@ -612,10 +616,9 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
     unsigned int ticket = 0;
     if (lane == 0) ticket = atomicAdd(&s_done[st], 1u);
     ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    if (ticket % nwarps == nwarps - 1 && t + p.nstage < ntile) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_tile<XT, S>(p, t0l + t + p.nstage, smem + st * stage_bytes, &s_bar[st], lane);
-    }
+    // the last warp to release refills the stage, after its collision (when
+    // its populations are no longer live)
+    const bool refill = ticket % nwarps == nwarps - 1 && t + p.nstage < ntile;
     if (active && ready) {
       const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
       T* out = dst + (long long)(unsigned)(crow0 + g.xc) * Gm::ROW;
@@ -649,11 +652,15 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
       ub_acc += m.ux;
       bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
       if (STATS) {
-        q[0] += m.ux; q[1] += m.uy; q[2] += m.uz;
-        q[3] += m.ux * m.ux; q[4] += m.uy * m.uy; q[5] += m.uz * m.uz;
-        q[6] += m.ux * m.uy; q[7] += m.ux * m.uz; q[8] += m.uy * m.uz;
+        qs[0 * 256] += m.ux; qs[1 * 256] += m.uy; qs[2 * 256] += m.uz;
+        qs[3 * 256] += m.ux * m.ux; qs[4 * 256] += m.uy * m.uy; qs[5 * 256] += m.uz * m.uz;
+        qs[6 * 256] += m.ux * m.uy; qs[7 * 256] += m.ux * m.uz; qs[8 * 256] += m.uy * m.uz;
         last_x = x;
       }
+    }
+    if (refill) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_tile<XT, S>(p, t0l + t + p.nstage, smem + st * stage_bytes, &s_bar[st], lane);
     }
     // advance to the next tile; flush the plane statistics when y changes
     const int y_now = g.y;
@@ -661,8 +668,15 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
       g.xc = 0;
       if (++g.zg == p.nzg) { g.zg = 0; ++g.y; }
     }
-    if (STATS && (g.y != y_now || t + 1 == ntile || flush_each_tile))
+    if (STATS && (g.y != y_now || t + 1 == ntile || flush_each_tile)) {
+      float q[9];
+#pragma unroll
+      for (int k = 0; k < 9; k++) {
+        q[k] = qs[k * 256];
+        qs[k * 256] = 0.f;
+      }
       flush_plane_stats(p, q, last_x, y_now, s_stats, lane, tid, nthreads);
+    }
   }
   finish_step(p, ub_acc, bad, late, s_ub, lane, warp, tid, nthreads);
 }
