@@ -409,20 +409,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// one test of the phase with the given parity (may suspend the thread briefly)
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
 // bounded wait for the phase with the given parity; false after `limit` polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t k = 0; k < limit; k++) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
+  for (uint32_t k = 0; k < limit; k++)
+    if (mbar_try(bar, parity)) return true;
   return false;
 }
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls (each may suspend ~us) before giving up
@@ -515,9 +517,11 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, long long t, uns
 // reads its cell's 19 populations from the staged rows (shared loads at
 // immediate offsets), collides in registers (moments, canopy velocity,
 // Smagorinsky tau, BGK + Guo) and stores whole lines to HBM.  A stage is
-// released when its last warp has consumed it (monotonic ticket); that warp
-// issues the refill at the end of its iteration, so no block-wide barrier
-// sits in the loop.
+// released when every warp has consumed it (monotonic per-stage count); the
+// refill is then claimed (compare-and-swap on the next fill index) by the
+// first warp that looks, at the top of its iteration or while it waits for
+// data, so the copies are issued by a warp with time to spare and no
+// block-wide barrier sits in the loop.
 template <int XT, int S, bool STATS>
 __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   using T = typename Store<S>::T;
@@ -532,6 +536,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   __shared__ float s_gx;
   __shared__ __align__(8) uint64_t s_bar[8];
   __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
+  __shared__ int s_fill;              // next tile (block-local index) to copy in
 
   const int tx = threadIdx.x;
   const int tid = threadIdx.y * XT + tx;
@@ -548,6 +553,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
       mbar_init(&s_bar[k], 1);
       s_done[k] = 0;
     }
+    s_fill = min(p.nstage, ntile);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (STATS) {
@@ -567,6 +573,26 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   T* dst = static_cast<T*>(p.dst) + Gm::G + tx;
   T* const dst0 = static_cast<T*>(p.dst) + Gm::G;  // slot G of direction 0, chunk-row 0
 
+  // Issue the next fill if its stage has been released by every warp and no
+  // other warp has claimed it (whole warp; lane 0 decides).
+  auto try_refill = [&]() {
+    int j = -1;
+    if (lane == 0) {
+      const int jn = *reinterpret_cast<volatile int*>(&s_fill);
+      if (jn < ntile) {
+        const unsigned need = (unsigned)(jn / p.nstage) * nwarps;
+        const unsigned done = *reinterpret_cast<volatile unsigned*>(&s_done[jn % p.nstage]);
+        if (done >= need && atomicCAS(&s_fill, jn, jn + 1) == jn) j = jn;
+      }
+    }
+    j = __shfl_sync(0xffffffffu, j, 0);
+    if (j >= 0) {
+      const int rs = j % p.nstage;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_tile<XT, S>(p, t0l + j, smem + rs * stage_bytes, &s_bar[rs], lane);
+    }
+  };
+
   TileGeom g = tile_geom(p, t0l);
   float ub_acc = 0.f;
   bool bad = false, late = false;
@@ -585,7 +611,15 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
     const int y = g.y;
     const bool active = (x < p.nx) && (z < p.nz);
 
-    const bool ready = mbar_wait(&s_bar[st], parity, WAIT_LIMIT);
+    try_refill();
+    bool ready = false;
+    for (uint32_t k = 0; k < WAIT_LIMIT; k++) {
+      if (__all_sync(0xffffffffu, mbar_try(&s_bar[st], parity))) {
+        ready = true;
+        break;
+      }
+      try_refill();
+    }
     if (!ready) late = true;
     float f[NQ];
     Macro m;
@@ -613,12 +647,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
     }
     // release the stage: the moments consumed every staged value of this warp
     __syncwarp();
-    unsigned int ticket = 0;
-    if (lane == 0) ticket = atomicAdd(&s_done[st], 1u);
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    // the last warp to release refills the stage, after its collision (when
-    // its populations are no longer live)
-    const bool refill = ticket % nwarps == nwarps - 1 && t + p.nstage < ntile;
+    if (lane == 0) atomicAdd(&s_done[st], 1u);
     if (active && ready) {
       const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
       T* out = dst + (long long)(unsigned)(crow0 + g.xc) * Gm::ROW;
@@ -657,10 +686,6 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
         qs[6 * 256] += m.ux * m.uy; qs[7 * 256] += m.ux * m.uz; qs[8 * 256] += m.uy * m.uz;
         last_x = x;
       }
-    }
-    if (refill) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_tile<XT, S>(p, t0l + t + p.nstage, smem + st * stage_bytes, &s_bar[st], lane);
     }
     // advance to the next tile; flush the plane statistics when y changes
     const int y_now = g.y;
