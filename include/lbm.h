@@ -192,6 +192,76 @@ void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(int32_t status);
 
+/* ---- ensembles of independent boxes ------------------------------------------
+ * Many independent domains ("boxes") of uneven sizes and canopy profiles, as in
+ * a wind-siting parameter sweep, advanced together.  The paper runs one domain
+ * at a time; the ensemble fills the GPU with many small ones: one kernel launch
+ * per step covers every box (each block works on one box's tiles with that
+ * box's parameters), and lbm_batch_step(n) replays n such launches as one CUDA
+ * graph.  The block shape (chunk width, hence the device layout) and the number
+ * of work items per launch are chosen by timing candidates at creation
+ * (tune_steps > 0), or by a size rule (tune_steps = 0).
+ *
+ * Every box is an ordinary lbm_ctx owned by the ensemble: lbm_batch_box()
+ * returns it for the readouts (lbm_get_f, lbm_get_macro, lbm_stats, lbm_mass,
+ * lbm_drive, lbm_save, lbm_load, lbm_set_f, lbm_sync), and even lbm_step on
+ * one box alone works; lbm_destroy on a box is a no-op (lbm_batch_destroy
+ * releases them).  The boxes use the ensemble's stream. */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct lbm_box {
+    lbm_grid grid;          /* any of the supported boundary combinations */
+    double tau0, cs;        /* as in lbm_create */
+    const double* lad;      /* ny leaf-area densities, or NULL */
+    lbm_forcing forcing;    /* u_bulk_target must be <= 0: no controller in an ensemble */
+    uint64_t seed;          /* initial perturbation seed of this box */
+} lbm_box;
+
+/* Device workspace an ensemble needs (the largest over the chunk widths the
+ * tuner may pick); 0 on invalid arguments. */
+size_t lbm_batch_workspace_bytes(int32_t nbox, const lbm_box* boxes, int32_t storage,
+                                 int32_t stats_xbins);
+
+/* Create nbox >= 1 boxes, all with the same storage type and statistics bins,
+ * initialised as lbm_create does with their own seed and the common
+ * init_perturb.  tune_steps > 0 times every candidate launch configuration over
+ * that many steps (the boxes are then re-initialised); cuda_stream NULL = legacy
+ * default stream.  workspace/workspace_bytes as in lbm_create. */
+lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
+                            int32_t stats_xbins, double init_perturb, int32_t tune_steps,
+                            void* cuda_stream, void* workspace, size_t workspace_bytes,
+                            lbm_batch** out);
+
+/* Enqueue n >= 0 steps of every box: one CUDA graph of n launches (built on
+ * first use for this n and reused).  Asynchronous.  Statistics must be on for
+ * all boxes or for none (lbm_batch_stats_reset). */
+lbm_status lbm_batch_step(lbm_batch* b, int32_t n);
+
+/* Wait for the stream and report device-side errors of any box. */
+lbm_status lbm_batch_sync(lbm_batch* b);
+
+/* lbm_stats_reset on every box. */
+lbm_status lbm_batch_stats_reset(lbm_batch* b, int32_t enable);
+
+/* Box i (0 <= i < nbox) as a context handle owned by the ensemble; NULL if out
+ * of range. */
+lbm_ctx* lbm_batch_box(lbm_batch* b, int32_t i);
+
+/* The launch configuration in use: chunk width (cells), blocks per launch and
+ * the measured milliseconds per step of the chosen candidate (0 if untuned). */
+lbm_status lbm_batch_tuning(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,
+                            double* ms_per_step);
+
+/* The tuner's record: for each candidate it timed (at most cap are written),
+ * its chunk width, blocks per launch and milliseconds per step (negative if it
+ * failed).  Returns the number of candidates timed (0 when untuned), -1 for
+ * b == NULL. */
+int32_t lbm_batch_candidates(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,
+                             double* ms_per_step, int32_t cap);
+
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

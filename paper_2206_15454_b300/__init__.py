@@ -39,6 +39,11 @@ class LbmForcing(C.Structure):
                 ("u_top", C.c_double * 3), ("u_in_profile", C.POINTER(C.c_double))]
 
 
+class LbmBox(C.Structure):
+    _fields_ = [("grid", LbmGrid), ("tau0", C.c_double), ("cs", C.c_double),
+                ("lad", C.POINTER(C.c_double)), ("forcing", LbmForcing), ("seed", C.c_uint64)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} (status {status})")
@@ -75,6 +80,28 @@ def lib():
             fn = getattr(L, name)
             fn.restype = st
             fn.argtypes = args
+        bp = C.POINTER(LbmBox)
+        L.lbm_batch_workspace_bytes.restype = C.c_size_t
+        L.lbm_batch_workspace_bytes.argtypes = [C.c_int32, bp, C.c_int32, C.c_int32]
+        L.lbm_batch_create.restype = st
+        L.lbm_batch_create.argtypes = [C.c_int32, bp, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                       vp, vp, C.c_size_t, C.POINTER(vp)]
+        for name, args in [("lbm_batch_step", [vp, C.c_int32]), ("lbm_batch_sync", [vp]),
+                           ("lbm_batch_stats_reset", [vp, C.c_int32]),
+                           ("lbm_batch_tuning", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                                 _DP])]:
+            fn = getattr(L, name)
+            fn.restype = st
+            fn.argtypes = args
+        L.lbm_batch_candidates.restype = C.c_int32
+        L.lbm_batch_candidates.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP,
+                                           C.c_int32]
+        L.lbm_batch_box.restype = vp
+        L.lbm_batch_box.argtypes = [vp, C.c_int32]
+        L.lbm_batch_destroy.restype = None
+        L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_batch_last_error.restype = C.c_char_p
+        L.lbm_batch_last_error.argtypes = [vp]
         L.lbm_steps_done.restype = C.c_int64
         L.lbm_steps_done.argtypes = [vp]
         L.lbm_destroy.restype = None
@@ -184,6 +211,63 @@ def lbm_destroy(ctx):
     lib().lbm_destroy(ctx)
 
 
+# ---- ensembles ----------------------------------------------------------------------
+
+def _batch_check(status, b, what):
+    if status != LBM_OK:
+        msg = lib().lbm_batch_last_error(b).decode() if b else ""
+        base = lib().lbm_status_string(status).decode()
+        raise LbmError(status, f"{what}: {base}{(' - ' + msg) if msg else ''}")
+
+
+def lbm_batch_workspace_bytes(boxes, storage: int, stats_xbins: int) -> int:
+    return int(lib().lbm_batch_workspace_bytes(len(boxes), boxes, storage, stats_xbins))
+
+
+def lbm_batch_create(boxes, storage, stats_xbins, init_perturb, tune_steps=0, stream_ptr=0,
+                     workspace=0, workspace_bytes=0):
+    b = C.c_void_p()
+    s = lib().lbm_batch_create(len(boxes), boxes, storage, stats_xbins, init_perturb, tune_steps,
+                               C.c_void_p(stream_ptr or None), C.c_void_p(workspace or None),
+                               workspace_bytes, C.byref(b))
+    _batch_check(s, None, "lbm_batch_create")
+    return b
+
+
+def lbm_batch_step(b, n):
+    _batch_check(lib().lbm_batch_step(b, int(n)), b, "lbm_batch_step")
+
+
+def lbm_batch_sync(b):
+    _batch_check(lib().lbm_batch_sync(b), b, "lbm_batch_sync")
+
+
+def lbm_batch_stats_reset(b, enable=True):
+    _batch_check(lib().lbm_batch_stats_reset(b, int(bool(enable))), b, "lbm_batch_stats_reset")
+
+
+def lbm_batch_box(b, i):
+    return C.c_void_p(lib().lbm_batch_box(b, int(i)))
+
+
+def lbm_batch_tuning(b):
+    xt, nb, ms = C.c_int32(), C.c_int32(), np.zeros(1)
+    _batch_check(lib().lbm_batch_tuning(b, C.byref(xt), C.byref(nb), _dp(ms)), b,
+                 "lbm_batch_tuning")
+    return int(xt.value), int(nb.value), float(ms[0])
+
+
+def lbm_batch_candidates(b, cap=64):
+    """[(chunk width, blocks per launch, ms per step)] for every candidate the tuner timed."""
+    xt, nb, ms = (C.c_int32 * cap)(), (C.c_int32 * cap)(), np.zeros(cap)
+    n = int(lib().lbm_batch_candidates(b, xt, nb, _dp(ms), cap))
+    return [(int(xt[k]), int(nb[k]), float(ms[k])) for k in range(min(max(n, 0), cap))]
+
+
+def lbm_batch_destroy(b):
+    lib().lbm_batch_destroy(b)
+
+
 # ---- convenience: one domain with a PyTorch-owned workspace and stream ---------------
 
 class Domain:
@@ -191,6 +275,8 @@ class Domain:
     ``workloads.Case`` (nx, ny, nz, bc_x/bc_y/bc_z pairs, tau0, cs, g, cd,
     canopy_x, u_bulk_target, ctrl_gain, u_top, stats_xbins, seed,
     init_perturb, lad, u_profile)."""
+
+    _owned = True
 
     def __init__(self, case, storage=LBM_F32, use_torch_workspace=True, stream=None):
         import torch
@@ -200,17 +286,8 @@ class Domain:
         self.case, self.storage = case, storage
         self.shape = (case.nz, case.ny, case.nx)
         self.cells = case.nx * case.ny * case.nz
-        g = LbmGrid(case.nx, case.ny, case.nz, *case.bc_x, *case.bc_y, *case.bc_z)
-        self._uprof = (None if case.u_profile is None
-                       else np.ascontiguousarray(case.u_profile, dtype=np.float64))
-        fo = LbmForcing()
-        fo.g[:] = [float(v) for v in case.g]
-        fo.cd = case.cd
-        fo.x_canopy_begin, fo.x_canopy_end = case.canopy_x
-        fo.u_bulk_target, fo.ctrl_gain = case.u_bulk_target, case.ctrl_gain
-        fo.u_top[:] = [float(v) for v in case.u_top]
-        fo.u_in_profile = _dp(self._uprof) if self._uprof is not None else _DP()
-        lad = None if case.lad is None else np.ascontiguousarray(case.lad, dtype=np.float64)
+        g, fo, lad, keep = _case_inputs(case)
+        self._keep = keep
         self.workspace = None
         ws_ptr, ws_bytes = 0, 0
         if use_torch_workspace:
@@ -225,10 +302,20 @@ class Domain:
                               case.seed, case.init_perturb, ws_ptr, ws_bytes)
         lbm_set_stream(self.ctx, self.stream.cuda_stream)
 
+    @classmethod
+    def _view(cls, ctx, case, storage, stream, owner):
+        """A box of an ensemble: same readouts, owned (and freed) by the ensemble."""
+        d = cls.__new__(cls)
+        d.case, d.storage, d.ctx, d.stream, d.workspace = case, storage, ctx, stream, None
+        d.shape = (case.nz, case.ny, case.nx)
+        d.cells = case.nx * case.ny * case.nz
+        d._owned, d._owner = False, owner
+        return d
+
     def close(self):
-        if getattr(self, "ctx", None) is not None:
+        if getattr(self, "ctx", None) is not None and self._owned:
             lbm_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
         self.workspace = None
 
     def __del__(self):
@@ -278,6 +365,100 @@ class Domain:
 
     def steps_done(self):
         return lbm_steps_done(self.ctx)
+
+
+def _case_inputs(case):
+    """lbm_grid, lbm_forcing and the LAD array of a case (plus arrays to keep alive)."""
+    g = LbmGrid(case.nx, case.ny, case.nz, *case.bc_x, *case.bc_y, *case.bc_z)
+    uprof = (None if case.u_profile is None
+             else np.ascontiguousarray(case.u_profile, dtype=np.float64))
+    fo = LbmForcing()
+    fo.g[:] = [float(v) for v in case.g]
+    fo.cd = case.cd
+    fo.x_canopy_begin, fo.x_canopy_end = case.canopy_x
+    fo.u_bulk_target, fo.ctrl_gain = case.u_bulk_target, case.ctrl_gain
+    fo.u_top[:] = [float(v) for v in case.u_top]
+    fo.u_in_profile = _dp(uprof) if uprof is not None else _DP()
+    lad = None if case.lad is None else np.ascontiguousarray(case.lad, dtype=np.float64)
+    return g, fo, lad, (uprof, lad)
+
+
+class Batch:
+    """An ensemble of independent boxes (cases with the same storage, statistics
+    bins and perturbation amplitude) advanced by one launch per step, replayed
+    as a CUDA graph.  ``box(i)`` gives a Domain view of box i."""
+
+    def __init__(self, cases, storage=LBM_F16_SHIFTED, tune_steps=0, use_torch_workspace=True,
+                 stream=None):
+        import torch
+
+        if isinstance(storage, str):
+            storage = STORAGE_NAMES[storage]
+        self.cases, self.storage = list(cases), storage
+        bins = {c.stats_xbins for c in self.cases}
+        amps = {c.init_perturb for c in self.cases}
+        if len(bins) != 1 or len(amps) != 1:
+            raise LbmError(LBM_ERR_ARG, "Batch: all boxes need the same stats_xbins and init_perturb")
+        self._keep = []
+        arr = (LbmBox * len(self.cases))()
+        for i, c in enumerate(self.cases):
+            g, fo, lad, keep = _case_inputs(c)
+            self._keep.append(keep)
+            arr[i].grid, arr[i].forcing = g, fo
+            arr[i].tau0, arr[i].cs, arr[i].seed = c.tau0, c.cs, c.seed
+            arr[i].lad = _dp(lad) if lad is not None else _DP()
+        self._boxes = arr
+        nbins, amp = bins.pop(), amps.pop()
+        self.workspace = None
+        ws_ptr, ws_bytes = 0, 0
+        if use_torch_workspace:
+            ws_bytes = lbm_batch_workspace_bytes(arr, storage, nbins)
+            if ws_bytes == 0:
+                raise LbmError(LBM_ERR_ARG, "lbm_batch_workspace_bytes: invalid boxes")
+            self.workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+            ws_ptr = self.workspace.data_ptr()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        self.b = lbm_batch_create(arr, storage, nbins, amp, tune_steps, self.stream.cuda_stream,
+                                  ws_ptr, ws_bytes)
+        self.boxes = [Domain._view(lbm_batch_box(self.b, i), c, storage, self.stream, self)
+                      for i, c in enumerate(self.cases)]
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def sync(self):
+        lbm_batch_sync(self.b)
+
+    def stats_reset(self, enable=True):
+        lbm_batch_stats_reset(self.b, enable)
+
+    def box(self, i):
+        return self.boxes[i]
+
+    def tuning(self):
+        return lbm_batch_tuning(self.b)
+
+    def candidates(self):
+        return lbm_batch_candidates(self.b)
+
+    @property
+    def cells(self):
+        return sum(c.nx * c.ny * c.nz for c in self.cases)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            for d in self.boxes:
+                d.ctx = None
+            lbm_batch_destroy(self.b)
+            self.b = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def build(force=False):

@@ -40,9 +40,10 @@ struct Shape {
   long long elems;      // elements per population set
 };
 
-Shape shape_of(const lbm_grid& gr, int storage) {
+// xt: chunk width, 0 = chunk_width(nx)
+Shape shape_of(const lbm_grid& gr, int storage, int xt = 0) {
   Shape s;
-  s.xt = chunk_width(gr.nx);
+  s.xt = xt ? xt : chunk_width(gr.nx);
   s.nxc = (gr.nx + s.xt - 1) / s.xt;
   s.g = 128 / (int)elem_bytes(storage);
   s.xtp = s.xt + 2 * s.g;
@@ -56,9 +57,9 @@ struct Layout {
       total;
 };
 
-Layout layout_of(const lbm_grid& g, int storage, int nbins) {
+Layout layout_of(const lbm_grid& g, int storage, int nbins, int xt = 0) {
   Layout L;
-  const Shape s = shape_of(g, storage);
+  const Shape s = shape_of(g, storage, xt);
   L.f_bytes = align_up((size_t)s.elems * elem_bytes(storage), kAlign);
   size_t off = 2 * L.f_bytes;
   L.stats_off = off;  off += align_up(sizeof(double) * 9 * nbins * g.ny, kAlign);
@@ -115,6 +116,7 @@ struct lbm_ctx {
   int nzg = 0;
   lbm_status status = LBM_OK;
   std::string err;
+  lbm_batch* batch = nullptr;  // owning ensemble, if this domain is one of its boxes
 
   void* fbuf(int k) const { return ws + (size_t)k * L.f_bytes; }
   double* stats() const { return reinterpret_cast<double*>(ws + L.stats_off); }
@@ -243,6 +245,10 @@ void plan_stages(lbm_ctx* c) {
                        (int)c->stage_smem);
   cudaFuncSetAttribute(step_kernel<XT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)c->stage_smem);
+  cudaFuncSetAttribute(batch_step_kernel<XT, S, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->stage_smem);
+  cudaFuncSetAttribute(batch_step_kernel<XT, S, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->stage_smem);
 }
 
 template <int XT, int S>
@@ -325,13 +331,21 @@ size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t storage, int32_t stats_
   return layout_of(*grid, storage, stats_xbins).total;
 }
 
-lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double* lad,
+}  // extern "C"
+
+namespace {
+// lbm_create with an optional chunk width (0: chunk_width(nx)); an ensemble
+// lays all its boxes out with one width so one kernel serves them all.
+lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double* lad,
                       const lbm_forcing* forcing, int32_t storage, int32_t stats_xbins,
                       uint64_t seed, double init_perturb, void* workspace,
-                      size_t workspace_bytes, lbm_ctx** out) {
+                      size_t workspace_bytes, int xt, cudaStream_t stream, lbm_ctx** out) {
   if (!out) return LBM_ERR_ARG;
   *out = nullptr;
-  const size_t need = lbm_workspace_bytes(grid, storage, stats_xbins);
+  if (xt != 0 && xt != 64 && xt != 128 && xt != 256) return LBM_ERR_ARG;
+  const size_t need = lbm_workspace_bytes(grid, storage, stats_xbins) == 0
+                          ? 0
+                          : layout_of(*grid, storage, stats_xbins, xt).total;
   if (need == 0 || !forcing || !(tau0 > 0.5) || !(cs >= 0.0) || !std::isfinite(tau0) ||
       !std::isfinite(cs) || !std::isfinite(init_perturb))
     return LBM_ERR_ARG;
@@ -354,9 +368,10 @@ lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double
   if (forcing->u_in_profile) c->uprof.assign(forcing->u_in_profile, forcing->u_in_profile + grid->ny);
   c->seed = seed;
   c->init_perturb = init_perturb;
-  c->sh = shape_of(*grid, storage);
+  c->sh = shape_of(*grid, storage, xt);
   c->cells = (long long)grid->nx * grid->ny * grid->nz;
-  c->L = layout_of(*grid, storage, stats_xbins);
+  c->L = layout_of(*grid, storage, stats_xbins, xt);
+  c->stream = stream;
 
   auto bail = [&](lbm_status s) {
     if (c->owns_ws && c->ws) cudaFree(c->ws);
@@ -409,6 +424,17 @@ lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double
     return bail(LBM_ERR_CUDA);
   *out = c;
   return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid* grid, double tau0, double cs, const double* lad,
+                      const lbm_forcing* forcing, int32_t storage, int32_t stats_xbins,
+                      uint64_t seed, double init_perturb, void* workspace,
+                      size_t workspace_bytes, lbm_ctx** out) {
+  return create_ctx(grid, tau0, cs, lad, forcing, storage, stats_xbins, seed, init_perturb,
+                    workspace, workspace_bytes, 0, nullptr, out);
 }
 
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
@@ -720,7 +746,7 @@ lbm_status lbm_get_macro_noalloc(lbm_ctx* c, double* rho, double* u, size_t n) {
 int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
 
 void lbm_destroy(lbm_ctx* c) {
-  if (!c) return;
+  if (!c || c->batch) return;  // boxes of an ensemble go with lbm_batch_destroy
   cudaStreamSynchronize(c->stream);
   if (c->macro_buf) cudaFree(c->macro_buf);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
@@ -745,5 +771,393 @@ const char* lbm_status_string(int32_t s) {
     default: return "unknown status";
   }
 }
+
+}  // extern "C"
+
+// ---- ensembles of independent boxes ----------------------------------------------------
+struct lbm_batch {
+  std::vector<lbm_ctx*> boxes;
+  int storage = 0, nbins = 1, xt = 0;
+  cudaStream_t stream = nullptr;   // the boxes' stream; graphs are launched on it
+  cudaStream_t capture = nullptr;  // private stream the graphs are captured on
+  char* ws = nullptr;
+  bool owns_ws = false;
+  std::vector<BatchWork> work;
+  BatchWork* work_dev = nullptr;
+  double tuned_ms = 0.0;
+  std::vector<double> tried;      // tuner record: (chunk width, blocks, ms per step) per candidate
+  struct Graph {
+    int n = 0;
+    bool stats = false;
+    std::vector<int> cur;         // each box's population set when the graph starts
+    StepParams* params = nullptr; // [2][nbox] device parameters, even / odd steps
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Graph> graphs;      // most recent last
+  std::string err;
+};
+
+namespace {
+
+constexpr int kBatchChunks[3] = {64, 128, 256};
+
+size_t batch_box_bytes(const lbm_box& b, int storage, int nbins, int xt) {
+  return align_up(layout_of(b.grid, storage, nbins, xt).total, kAlign);
+}
+
+bool batch_args_ok(int32_t nbox, const lbm_box* boxes, int32_t storage, int32_t nbins) {
+  if (nbox < 1 || !boxes || storage < 0 || storage > 2) return false;
+  for (int i = 0; i < nbox; i++) {
+    if (lbm_workspace_bytes(&boxes[i].grid, storage, nbins) == 0) return false;
+    if (boxes[i].forcing.u_bulk_target > 0.0) return false;
+  }
+  return true;
+}
+
+void free_graphs(lbm_batch* b) {
+  for (auto& g : b->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.params) cudaFree(g.params);
+  }
+  b->graphs.clear();
+}
+
+void free_boxes(lbm_batch* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  free_graphs(b);
+  for (lbm_ctx* c : b->boxes) {
+    if (!c) continue;
+    c->batch = nullptr;
+    lbm_destroy(c);
+  }
+  b->boxes.clear();
+  if (b->work_dev) cudaFree(b->work_dev);
+  b->work_dev = nullptr;
+}
+
+// Boxes with chunk width xt in the ensemble's workspace (or their own memory).
+lbm_status make_boxes(lbm_batch* b, int32_t nbox, const lbm_box* boxes, double init_perturb,
+                      int xt) {
+  size_t off = 0;
+  for (int i = 0; i < nbox; i++) {
+    const lbm_box& x = boxes[i];
+    const size_t bytes = batch_box_bytes(x, b->storage, b->nbins, xt);
+    lbm_ctx* c = nullptr;
+    const lbm_status s =
+        create_ctx(&x.grid, x.tau0, x.cs, x.lad, &x.forcing, b->storage, b->nbins, x.seed,
+                   init_perturb, b->ws ? b->ws + off : nullptr, b->ws ? bytes : 0, xt, b->stream, &c);
+    if (s != LBM_OK) {
+      b->err = "lbm_batch_create: box " + std::to_string(i) + ": " + lbm_status_string(s);
+      return s;
+    }
+    c->batch = b;
+    b->boxes.push_back(c);
+    off += bytes;
+  }
+  b->xt = xt;
+  return LBM_OK;
+}
+
+// Work items: every box's tiles cut into runs of about `per` tiles, one run per block.
+lbm_status make_work(lbm_batch* b, int waves) {
+  long long total = 0;
+  for (lbm_ctx* c : b->boxes) total += make_params(c).ntiles;
+  const lbm_ctx* c0 = b->boxes[0];
+  const long long resident = (long long)c0->sm_count * std::max(1, c0->blocks_per_sm);
+  const long long per = std::max<long long>(1, (total + waves * resident - 1) / (waves * resident));
+  b->work.clear();
+  for (int i = 0; i < (int)b->boxes.size(); i++) {
+    const long long nt = make_params(b->boxes[i]).ntiles;
+    const long long items = (nt + per - 1) / per;
+    for (long long k = 0; k < items; k++) {
+      BatchWork w;
+      w.box = i;
+      w.t0 = k * nt / items;
+      w.ntile = (int)((k + 1) * nt / items - w.t0);
+      b->work.push_back(w);
+    }
+  }
+  if (b->work_dev) cudaFree(b->work_dev);
+  b->work_dev = nullptr;
+  free_graphs(b);
+  if (cudaMalloc(&b->work_dev, sizeof(BatchWork) * b->work.size()) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "lbm_batch: cudaMalloc of the work list failed";
+    return LBM_ERR_OOM;
+  }
+  if (cudaMemcpy(b->work_dev, b->work.data(), sizeof(BatchWork) * b->work.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    b->err = "lbm_batch: copy of the work list failed";
+    return LBM_ERR_CUDA;
+  }
+  return LBM_OK;
+}
+
+// The graph of n launches starting from the boxes' current population sets.
+lbm_status batch_graph(lbm_batch* b, int n, bool stats, cudaGraphExec_t* exec) {
+  const int nb = (int)b->boxes.size();
+  std::vector<int> cur(nb);
+  for (int i = 0; i < nb; i++) cur[i] = b->boxes[i]->cur;
+  for (auto& g : b->graphs)
+    if (g.n == n && g.stats == stats && g.cur == cur) {
+      *exec = g.exec;
+      return LBM_OK;
+    }
+  if (b->graphs.size() >= 4) {  // keep the cache small
+    if (b->graphs.front().exec) cudaGraphExecDestroy(b->graphs.front().exec);
+    if (b->graphs.front().params) cudaFree(b->graphs.front().params);
+    b->graphs.erase(b->graphs.begin());
+  }
+  lbm_batch::Graph g;
+  g.n = n;
+  g.stats = stats;
+  g.cur = cur;
+  std::vector<StepParams> hp(2 * (size_t)nb);
+  for (int i = 0; i < nb; i++) {
+    lbm_ctx* c = b->boxes[i];
+    hp[i] = make_params(c);
+    c->cur = 1 - c->cur;
+    hp[nb + i] = make_params(c);
+    c->cur = 1 - c->cur;
+  }
+  if (cudaMalloc(&g.params, sizeof(StepParams) * hp.size()) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "lbm_batch_step: cudaMalloc of the box parameters failed";
+    return LBM_ERR_OOM;
+  }
+  if (cudaMemcpy(g.params, hp.data(), sizeof(StepParams) * hp.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    cudaFree(g.params);
+    b->err = "lbm_batch_step: copy of the box parameters failed";
+    return LBM_ERR_CUDA;
+  }
+  const lbm_ctx* c0 = b->boxes[0];
+  cudaGraph_t graph = nullptr;
+  cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaError_t e = cudaStreamBeginCapture(b->capture, mode);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < n; k++) {
+      const StepParams* P = g.params + (k & 1) * nb;
+      dispatch(c0, [&](auto xt, auto s) {
+        constexpr int XT = decltype(xt)::value, S = decltype(s)::value;
+        if (stats)
+          batch_step_kernel<XT, S, true><<<(int)b->work.size(), c0->block, c0->stage_smem,
+                                           b->capture>>>(P, b->work_dev);
+        else
+          batch_step_kernel<XT, S, false><<<(int)b->work.size(), c0->block, c0->stage_smem,
+                                            b->capture>>>(P, b->work_dev);
+      });
+    }
+    e = cudaStreamEndCapture(b->capture, &graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g.params);
+    b->err = std::string("lbm_batch_step: CUDA graph capture failed: ") + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+  }
+  b->graphs.push_back(g);
+  *exec = g.exec;
+  return LBM_OK;
+}
+
+lbm_status batch_run(lbm_batch* b, int n) {
+  if (n == 0) return LBM_OK;
+  bool stats = b->boxes[0]->stats_on;
+  for (lbm_ctx* c : b->boxes) {
+    if (c->status != LBM_OK) {
+      b->err = "lbm_batch_step: a box holds an earlier error: " + c->err;
+      return LBM_ERR_STATE;
+    }
+    if (c->stats_on != stats) {
+      b->err = "lbm_batch_step: statistics must be on for every box or for none";
+      return LBM_ERR_ARG;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  const lbm_status s = batch_graph(b, n, stats, &exec);
+  if (s != LBM_OK) return s;
+  if (cudaGraphLaunch(exec, b->stream) != cudaSuccess) {
+    b->err = std::string("lbm_batch_step: graph launch failed: ") +
+             cudaGetErrorString(cudaGetLastError());
+    return LBM_ERR_CUDA;
+  }
+  for (lbm_ctx* c : b->boxes) {
+    if (n & 1) c->cur = 1 - c->cur;
+    c->steps += n;
+    if (c->stats_on) c->stats_samples += n;
+  }
+  return LBM_OK;
+}
+
+// Milliseconds per step of the current configuration over `steps` steps.
+double batch_time(lbm_batch* b, int steps) {
+  if (batch_run(b, 2) != LBM_OK) return -1.0;  // warm-up, builds nothing reused
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, b->stream);
+  const lbm_status s = batch_run(b, steps);
+  cudaEventRecord(e1, b->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  free_graphs(b);
+  return s == LBM_OK ? (double)ms / steps : -1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_workspace_bytes(int32_t nbox, const lbm_box* boxes, int32_t storage,
+                                 int32_t stats_xbins) {
+  if (!batch_args_ok(nbox, boxes, storage, stats_xbins)) return 0;
+  size_t best = 0;
+  for (int xt : kBatchChunks) {
+    size_t sum = 0;
+    for (int i = 0; i < nbox; i++) sum += batch_box_bytes(boxes[i], storage, stats_xbins, xt);
+    best = std::max(best, sum);
+  }
+  return best;
+}
+
+lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
+                            int32_t stats_xbins, double init_perturb, int32_t tune_steps,
+                            void* cuda_stream, void* workspace, size_t workspace_bytes,
+                            lbm_batch** out) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (!batch_args_ok(nbox, boxes, storage, stats_xbins) || tune_steps < 0 ||
+      !std::isfinite(init_perturb))
+    return LBM_ERR_ARG;
+  const size_t need = lbm_batch_workspace_bytes(nbox, boxes, storage, stats_xbins);
+  if (workspace && workspace_bytes < need) return LBM_ERR_OOM;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LBM_ERR_ARG;
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ERR_OOM;
+  b->storage = storage;
+  b->nbins = stats_xbins;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](lbm_status s) {
+    free_boxes(b);
+    if (b->owns_ws && b->ws) cudaFree(b->ws);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->capture = nullptr;
+    return bail(LBM_ERR_CUDA);
+  }
+  if (workspace) {
+    b->ws = static_cast<char*>(workspace);
+  } else {
+    if (cudaMalloc(&b->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      b->ws = nullptr;
+      return bail(LBM_ERR_OOM);
+    }
+    b->owns_ws = true;
+  }
+  int max_nx = 0;
+  for (int i = 0; i < nbox; i++) max_nx = std::max(max_nx, boxes[i].grid.nx);
+  // size rule: the widest chunk that does not exceed the longest row
+  int best_xt = chunk_width(max_nx), best_waves = 8;
+  double best_ms = 0.0;
+  if (tune_steps > 0) {
+    best_ms = 1e300;
+    for (int xt : kBatchChunks) {
+      if (xt > 2 * chunk_width(max_nx)) continue;
+      lbm_status s = make_boxes(b, nbox, boxes, init_perturb, xt);
+      if (s != LBM_OK) return bail(s);
+      for (int waves : {2, 4, 8, 16}) {
+        if ((s = make_work(b, waves)) != LBM_OK) return bail(s);
+        const double ms = batch_time(b, tune_steps);
+        b->tried.insert(b->tried.end(), {(double)xt, (double)b->work.size(), ms});
+        if (ms > 0.0 && ms < best_ms) {
+          best_ms = ms;
+          best_xt = xt;
+          best_waves = waves;
+        }
+      }
+      free_boxes(b);
+    }
+  }
+  if (best_ms >= 1e300) best_ms = 0.0;  // no candidate could be timed: the size rule stands
+  lbm_status s = make_boxes(b, nbox, boxes, init_perturb, best_xt);
+  if (s == LBM_OK) s = make_work(b, best_waves);
+  if (s != LBM_OK) return bail(s);
+  b->tuned_ms = best_ms;
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int32_t n) {
+  if (!b || n < 0) return LBM_ERR_ARG;
+  return batch_run(b, n);
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+  if (!b) return LBM_ERR_ARG;
+  for (lbm_ctx* c : b->boxes) {
+    const lbm_status s = lbm_sync(c);
+    if (s != LBM_OK) {
+      b->err = "lbm_batch_sync: " + c->err;
+      return s;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_stats_reset(lbm_batch* b, int32_t enable) {
+  if (!b) return LBM_ERR_ARG;
+  for (lbm_ctx* c : b->boxes) {
+    const lbm_status s = lbm_stats_reset(c, enable);
+    if (s != LBM_OK) return s;
+  }
+  return LBM_OK;
+}
+
+lbm_ctx* lbm_batch_box(lbm_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->boxes.size()) return nullptr;
+  return b->boxes[i];
+}
+
+lbm_status lbm_batch_tuning(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,
+                            double* ms_per_step) {
+  if (!b) return LBM_ERR_ARG;
+  if (chunk_width) *chunk_width = b->xt;
+  if (blocks) *blocks = (int32_t)b->work.size();
+  if (ms_per_step) *ms_per_step = b->tuned_ms;
+  return LBM_OK;
+}
+
+int32_t lbm_batch_candidates(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,
+                             double* ms_per_step, int32_t cap) {
+  if (!b) return -1;
+  const int n = (int)(b->tried.size() / 3);
+  for (int k = 0; k < n && k < cap; k++) {
+    if (chunk_width) chunk_width[k] = (int32_t)b->tried[3 * k];
+    if (blocks) blocks[k] = (int32_t)b->tried[3 * k + 1];
+    if (ms_per_step) ms_per_step[k] = b->tried[3 * k + 2];
+  }
+  return n;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  free_boxes(b);
+  if (b->owns_ws && b->ws) cudaFree(b->ws);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : ""; }
 
 }  // extern "C"

@@ -364,16 +364,16 @@ __device__ __forceinline__ void flush_plane_stats(const StepParams& p, float* q,
 // Step epilogue: health flags and this block's share of the bulk velocity.
 __device__ __forceinline__ void finish_step(const StepParams& p, float ub_acc, bool bad, bool late,
                                             float* s_ub, int lane, int warp, int tid,
-                                            int nthreads) {
+                                            int nthreads, int part) {
   if (bad) atomicOr(&p.state->nan_flag, 1u);
   if (late) atomicOr(&p.state->timeout_flag, 1u);
   const float w = warp_sum(ub_acc);
   if (lane == 0) s_ub[warp] = w;
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && part >= 0) {
     double s = 0.0;
     for (int kk = 0; kk < (nthreads + 31) / 32; kk++) s += (double)s_ub[kk];
-    p.ub_part[(long long)p.slot_write * MAX_BLOCKS + blockIdx.x] = s;
+    p.ub_part[(long long)p.slot_write * MAX_BLOCKS + part] = s;
   }
 }
 
@@ -523,7 +523,7 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, long long t, uns
 // data, so the copies are issued by a warp with time to spare and no
 // block-wide barrier sits in the loop.
 template <int XT, int S, bool STATS>
-__global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
+__device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part) {
   using T = typename Store<S>::T;
   using Gm = Geo<XT, S>;
   using St = Stage<XT, S>;
@@ -544,9 +544,6 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned int nwarps = (unsigned int)nthreads / 32;
   const int stage_bytes = (int)blockDim.y * NQ * St::SROW * (int)sizeof(T);
-
-  const long long t0l = (long long)blockIdx.x * p.ntiles / gridDim.x;
-  const int ntile = (int)((long long)(blockIdx.x + 1) * p.ntiles / gridDim.x - t0l);
 
   if (tid == 0) {
     for (int k = 0; k < p.nstage; k++) {
@@ -703,7 +700,40 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
       flush_plane_stats(p, q, last_x, y_now, s_stats, lane, tid, nthreads);
     }
   }
-  finish_step(p, ub_acc, bad, late, s_ub, lane, warp, tid, nthreads);
+  finish_step(p, ub_acc, bad, late, s_ub, lane, warp, tid, nthreads, part);
+}
+
+// One domain: block b takes the b-th of gridDim.x equal runs of its tiles.
+template <int XT, int S, bool STATS>
+__global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
+  const long long t0l = (long long)blockIdx.x * p.ntiles / gridDim.x;
+  const int ntile = (int)((long long)(blockIdx.x + 1) * p.ntiles / gridDim.x - t0l);
+  step_tiles<XT, S, STATS>(p, t0l, ntile, blockIdx.x);
+}
+
+// Many independent domains (an ensemble of boxes) in one launch: work item
+// w = (box, first tile, tiles) per block; the block runs the same tile loop
+// with its box's parameters copied to shared memory.
+struct BatchWork {
+  int box, ntile;
+  long long t0;
+};
+
+template <int XT, int S, bool STATS>
+__global__ void __launch_bounds__(256, 3) batch_step_kernel(const StepParams* __restrict__ boxes,
+                                                            const BatchWork* __restrict__ work) {
+  __shared__ __align__(16) StepParams s_p;
+  const BatchWork w = work[blockIdx.x];
+  {
+    static_assert(sizeof(StepParams) % 4 == 0, "copied as words");
+    const unsigned* src = reinterpret_cast<const unsigned*>(boxes + w.box);
+    unsigned* dst = reinterpret_cast<unsigned*>(&s_p);
+    for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < (int)(sizeof(StepParams) / 4);
+         k += blockDim.x * blockDim.y)
+      dst[k] = src[k];
+  }
+  __syncthreads();
+  step_tiles<XT, S, STATS>(s_p, w.t0, w.ntile, -1);
 }
 
 // ---- ghost slots from the cells (after init, set_f) ----------------------------------

@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     for n in declared:
         assert hasattr(P.lib(), n)
-        assert hasattr(P, n) or n in ("lbm_last_error", "lbm_status_string")
+        assert hasattr(P, n) or n in ("lbm_last_error", "lbm_status_string", "lbm_batch_last_error")
 
 
 def _grid(nx=64, ny=32, nz=16, bc=(0, 0, 1, 2, 0, 0)):
@@ -105,3 +105,37 @@ def test_structs_match_the_header():
     # lbm_grid: 9 int32; lbm_forcing: 3+1 doubles, 2 int32, 2+3 doubles, 1 pointer
     assert C.sizeof(P.LbmGrid) == 36
     assert C.sizeof(P.LbmForcing) == 8 * 4 + 8 + 8 * 5 + 8
+
+
+def test_ensemble_arguments_checked_without_a_device():
+    cases = W.ensemble_boxes(n_boxes=3, ny=16, nz=8, nx_range=(40, 90), seed=3)
+    arr = (P.LbmBox * 3)()
+    keep = []
+    for i, c in enumerate(cases):
+        g, fo, lad, k = P._case_inputs(c)
+        keep.append(k)
+        arr[i].grid, arr[i].forcing, arr[i].tau0, arr[i].cs, arr[i].seed = g, fo, c.tau0, c.cs, 1
+        arr[i].lad = P._dp(lad)
+    n = P.lbm_batch_workspace_bytes(arr, P.LBM_F16_SHIFTED, 1)
+    # at least the sum of the boxes alone (the tuner may pick another chunk width)
+    alone = sum(P.lbm_workspace_bytes(arr[i].grid, P.LBM_F16_SHIFTED, 1) for i in range(3))
+    assert n >= alone > 0
+    assert P.lbm_batch_workspace_bytes(arr, 7, 1) == 0
+    arr[1].forcing.u_bulk_target = 0.05  # no controller inside an ensemble
+    assert P.lbm_batch_workspace_bytes(arr, P.LBM_F16_SHIFTED, 1) == 0
+    b = C.c_void_p()
+    assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, 0, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
+    arr[1].forcing.u_bulk_target = 0.0
+    assert P.lib().lbm_batch_create(0, arr, 1, 1, 0.0, 0, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
+    assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, -1, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
+    assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, 0, None, C.c_void_p(4096), 16,
+                                    C.byref(b)) == P.LBM_ERR_OOM
+    assert P.lib().lbm_batch_step(None, 1) == P.LBM_ERR_ARG
+    assert P.lib().lbm_batch_box(None, 0) is None
+    P.lib().lbm_batch_destroy(None)
+    assert P.lib().lbm_batch_candidates(None, None, None, None, 0) == -1
+
+
+def test_box_struct_matches_the_header():
+    # lbm_box: lbm_grid (36 B, padded to 40), 2 doubles, 1 pointer, lbm_forcing, uint64
+    assert C.sizeof(P.LbmBox) == 40 + 16 + 8 + C.sizeof(P.LbmForcing) + 8
