@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--storage", choices=["f32", "f16s", "bf16s"], default="f32")
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16 storage legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-box ensemble leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile", metavar="NXxNYxNZ", default=None,
                     help="run a few steps of the channel workload at this size and exit "
@@ -204,6 +205,38 @@ def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
     return d, case, total_ms, per_launch_ms
 
 
+def time_ensemble(P, W, steps, warmup, hbm):
+    """The 64-box canopy ensemble (96..160 x 64 x 64 cells each, FP16-shifted):
+    tuned at creation, then `steps` steps replayed as one CUDA graph."""
+    import torch
+
+    b = P.Batch(W.ensemble_boxes(), P.LBM_F16_SHIFTED, tune_steps=10)
+    b.step(warmup)
+    b.sync()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(b.stream)
+    b.step(steps)
+    t1.record(b.stream)
+    torch.cuda.synchronize()
+    b.sync()
+    ms = t0.elapsed_time(t1) / steps
+    cells = b.cells
+    xt, blocks, tuned_ms = b.tuning()
+    padded = sum(c.ny * c.nz * ((c.nx + xt - 1) // xt) * xt for c in b.cases)
+    ach = P.BYTES_PER_LUP[P.LBM_F16_SHIFTED] * cells / (ms * 1e-3) / 1e9
+    out = {"value": round(cells / ms / 1e3, 1), "unit": "MLUPS", "ms_per_step": ms,
+           "steps": steps, "warmup": warmup, "boxes": len(b.cases), "cells": cells,
+           "storage": "f16s", "timing": "one CUDA graph of all steps, CUDA events on its stream",
+           "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(ach / hbm, 4), "traffic": None},
+           "tuning": {"chunk_width": xt, "blocks_per_launch": blocks,
+                      "padded_cells_fraction": round(cells / padded, 4),
+                      "candidates": [{"chunk_width": c[0], "blocks": c[1], "ms_per_step": c[2]}
+                                     for c in b.candidates()]}}
+    b.close()
+    return out
+
+
 def e2e_run(P, d, steps):
     """Per step, through the public API: enqueue the step, then read the step's
     result (the time-averaged plane statistics) into a host buffer; the call
@@ -310,6 +343,8 @@ def run_ours(args):
                                       "unit": "GB/s", "frac": round(ach / hbm, 4),
                                       "traffic": measured_traffic(name, cells)},
                          "rel_l2_f_vs_f32_after_100_steps": err}
+    if not args.no_ensemble:
+        res["ensemble"] = time_ensemble(P, W, min(args.steps, 1000), max(args.warmup, 3), hbm)
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(W.channel_les, args.cpu_seconds)
     if rank == 0:
