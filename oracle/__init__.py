@@ -56,6 +56,9 @@ def lib():
         _lib.olbm_stats.restype = C.c_int64
         _lib.olbm_stats.argtypes = [C.c_void_p, dp]
         _lib.olbm_drive.argtypes = [C.c_void_p, dp, dp]
+        _lib.olbm_fields.argtypes = [C.c_void_p, dp, dp, dp]
+        _lib.olbm_set_layer0_accel.restype = C.c_int
+        _lib.olbm_set_layer0_accel.argtypes = [C.c_void_p, dp]
         _lib.olbm_steps_done.restype = C.c_int64
         _lib.olbm_steps_done.argtypes = [C.c_void_p]
         _lib.olbm_lattice.argtypes = [C.POINTER(C.c_int32), dp]
@@ -209,6 +212,47 @@ class Oracle:
 
     def steps_done(self):
         return int(lib().olbm_steps_done(self._h))
+
+    # ---- learned first-layer correction (inputs and application) ----------------
+
+    def fields(self):
+        """rho, u and |S| that the next step computes (no layer-0 correction)."""
+        rho = np.zeros(self.shape)
+        u = np.zeros((3,) + self.shape)
+        strain = np.zeros(self.shape)
+        lib().olbm_fields(self._h, _dp(rho), _dp(u), _dp(strain))
+        return rho, u, strain
+
+    def features(self):
+        """Correction inputs per first-cell column, rows in (z, x) order:
+        u_x at y = 0, 1, 2, |S| at y = 0, 1, 2, leaf-area density at y = 0, 1, 2
+        (zero outside the canopy's x-range)."""
+        _, u, strain = self.fields()
+        c = self.case
+        nz, nx = c.nz, c.nx
+        lad = np.zeros((3, nx))
+        if c.lad is not None:
+            x = np.arange(nx)
+            inside = (x >= c.canopy_x[0]) & (x < c.canopy_x[1])
+            for y in range(3):
+                lad[y] = np.where(inside, c.lad[y], 0.0)
+        X = np.zeros((nz, nx, 9))
+        for y in range(3):
+            X[:, :, y] = u[0, :, y, :]
+            X[:, :, 3 + y] = strain[:, y, :]
+            X[:, :, 6 + y] = lad[y][None, :]
+        return X.reshape(nz * nx, 9)
+
+    def set_layer0_accel(self, a):
+        """Extra (x, z) acceleration of the cells at y = 0, shape (nz, nx, 2),
+        applied by every following step; None switches it off."""
+        if a is None:
+            lib().olbm_set_layer0_accel(self._h, C.POINTER(C.c_double)())
+            return
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(self.case.nz, self.case.nx, 2)
+        self._accel0 = a
+        if lib().olbm_set_layer0_accel(self._h, _dp(a)) != 0:
+            raise MemoryError("olbm_set_layer0_accel")
 
 
 def omp_threads() -> int:

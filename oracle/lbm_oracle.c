@@ -82,6 +82,7 @@ struct olbm {
     int64_t stats_samples;
     double* acc;       /* [9][xbins][ny]: sums of u,v,w,uu,vv,ww,uv,uw,vw */
     double* cnt;       /* [xbins][ny] number of cell samples */
+    double* accel0;    /* [z][x][2] extra (x, z) acceleration of the cells at y = 0, or NULL */
 };
 
 static size_t cell_index(const olbm* s, int x, int y, int z)
@@ -345,6 +346,7 @@ void olbm_destroy(olbm* s)
     free(s->cell_u);
     free(s->acc);
     free(s->cnt);
+    free(s->accel0);
     free(s);
 }
 
@@ -361,7 +363,15 @@ static void one_step(olbm* s)
             for (int x = 0; x < p->nx; x++) {
                 double fin[Q], fout[Q], rho, u[3];
                 for (int i = 0; i < Q; i++) fin[i] = pull_population(s, s->f, i, x, y, z);
-                olbm_collide_cell(fin, g, drag_factor(s, x, y), p->tau0, p->cs, fout, &rho, u);
+                /* the learned first-layer correction enters as extra driving
+                 * acceleration of the cells at y = 0 */
+                double gc[3] = {g[0], g[1], g[2]};
+                if (y == 0 && s->accel0) {
+                    const double* a = s->accel0 + 2 * ((size_t)z * p->nx + x);
+                    gc[0] += a[0];
+                    gc[2] += a[1];
+                }
+                olbm_collide_cell(fin, gc, drag_factor(s, x, y), p->tau0, p->cs, fout, &rho, u);
                 size_t c = cell_index(s, x, y, z);
                 for (int i = 0; i < Q; i++) s->ftmp[(size_t)i * s->n + c] = fout[i];
                 s->cell_rho[c] = rho;
@@ -422,6 +432,65 @@ void olbm_macro(const olbm* s, double* rho_out, double* u_out)
                 rho_out[c] = rho;
                 for (int a = 0; a < 3; a++) u_out[(size_t)a * s->n + c] = u[a];
             }
+}
+
+void olbm_fields(const olbm* s, double* rho_out, double* u_out, double* strain_out)
+{
+    const olbm_params* p = &s->p;
+    double g[3];
+    drive_for_next_step(s, g);
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                double fin[Q];
+                for (int i = 0; i < Q; i++) fin[i] = pull_population(s, s->f, i, x, y, z);
+                /* the same moments, velocity and non-equilibrium flux as the
+                 * collision of the next step (Eqs. density, momentum, tensor) */
+                double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < Q; i++) {
+                    rho += fin[i];
+                    for (int a = 0; a < 3; a++) m[a] += fin[i] * CV[i][a];
+                }
+                double v[3], u[3];
+                for (int a = 0; a < 3; a++) v[a] = (m[a] + 0.5 * rho * g[a]) / rho;
+                olbm_canopy_velocity(v, drag_factor(s, x, y), u);
+                double feq[Q];
+                olbm_feq(rho, u, feq);
+                double pi[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = 0; i < Q; i++) {
+                    double d = fin[i] - feq[i];
+                    pi[0] += CV[i][0] * CV[i][0] * d;
+                    pi[1] += CV[i][1] * CV[i][1] * d;
+                    pi[2] += CV[i][2] * CV[i][2] * d;
+                    pi[3] += CV[i][0] * CV[i][1] * d;
+                    pi[4] += CV[i][0] * CV[i][2] * d;
+                    pi[5] += CV[i][1] * CV[i][2] * d;
+                }
+                double q = sqrt(pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
+                                2.0 * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]));
+                double tau = olbm_tau_total(p->tau0, p->cs, rho, pi);
+                /* Pi_neq = -2 rho c_s^2 tau S (Chapman-Enskog, the relation
+                 * behind Eq. strain), so |S| = sqrt(2 S:S) = sqrt(2) Q^1/2 / (2 rho c_s^2 tau) */
+                size_t c = cell_index(s, x, y, z);
+                if (rho_out) rho_out[c] = rho;
+                if (u_out)
+                    for (int a = 0; a < 3; a++) u_out[(size_t)a * s->n + c] = u[a];
+                if (strain_out) strain_out[c] = sqrt(2.0) * q / (2.0 * rho * CS2 * tau);
+            }
+}
+
+int olbm_set_layer0_accel(olbm* s, const double* a)
+{
+    if (a == NULL) {
+        free(s->accel0);
+        s->accel0 = NULL;
+        return 0;
+    }
+    size_t m = 2 * (size_t)s->p.nx * s->p.nz;
+    if (!s->accel0) s->accel0 = (double*)malloc(sizeof(double) * m);
+    if (!s->accel0) return -1;
+    memcpy(s->accel0, a, sizeof(double) * m);
+    return 0;
 }
 
 double olbm_mass(const olbm* s)

@@ -72,6 +72,15 @@ void olbm_set_f(olbm* s, const double* f);
 /* Density and force-corrected velocity that the next step would compute,
  * rho[z][y][x] and u[3][z][y][x]. */
 void olbm_macro(const olbm* s, double* rho, double* u);
+/* Density, velocity and strain-rate magnitude |S| = sqrt(2 S:S) that the
+ * next step computes, per cell [z][y][x] (u: [3][z][y][x]); |S| follows from
+ * the non-equilibrium momentum flux, Pi_neq = -2 rho c_s^2 tau_total S.
+ * Any output may be NULL.  The layer-0 correction is not included. */
+void olbm_fields(const olbm* s, double* rho, double* u, double* strain);
+/* Learned first-layer correction: an extra driving acceleration (x and z
+ * components, [z][x][2]) of the cells at y = 0 in every following step;
+ * NULL switches it off.  Returns 0, or -1 if memory ran out. */
+int olbm_set_layer0_accel(olbm* s, const double* a);
 /* Global mass, sum over cells and directions of the stored populations. */
 double olbm_mass(const olbm* s);
 /* Statistics window: reset (and enable) accumulation, read averages.
