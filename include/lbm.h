@@ -192,6 +192,63 @@ void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(int32_t status);
 
+/* ---- learned first-layer correction --------------------------------------------
+ * The paper has no learned component.  This is a near-wall/canopy correction
+ * of the cells next to the ground at coarse resolution: a network maps, for
+ * every first-cell column (x, z), the streamwise velocity u_x, the strain-rate
+ * magnitude |S| = sqrt(2 S:S) (from Pi_neq = -2 rho c_s^2 tau_total S) and the
+ * leaf-area density of the cells y = 0, 1, 2 (9 inputs) to
+ * (du_x, du_z, dtau_x, dtau_z); the next step then drives cell (x, 0, z) with
+ * the extra acceleration (lam*du_x - dtau_x, 0, lam*du_z - dtau_z) in its Guo
+ * force.  The network is 9-64-64-64-4 with tanh hidden layers, BF16 weights and
+ * activations, FP32 accumulation (tensor cores for inference), trained with
+ * Adam on the mean squared error of standardised targets.  It is meant to be
+ * trained on data the plain method produces on a 2x finer grid, coarsened; the
+ * plain step (no correction) stays the fallback.
+ *
+ * Parameters travel as one FP32 vector of 9246 values, rows = outputs,
+ * row-major: W1[64][9] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[4][64]
+ * b4[4], then x_mean[9] x_std[9] y_mean[4] y_std[4] (inputs are standardised
+ * as (x - x_mean)/x_std, outputs are y_mean + y_std*o).  Feature rows are 9
+ * floats in the order above, output rows 4 floats; columns are ordered (z, x). */
+typedef struct lbm_mlp lbm_mlp;
+
+/* A network with Glorot-uniform weights drawn from SplitMix64(seed), zero
+ * biases and unit normalisation; it works on cuda_stream (NULL = legacy
+ * default stream). */
+lbm_status lbm_mlp_create(uint64_t seed, void* cuda_stream, lbm_mlp** out);
+/* Copy the 9246 parameters out / in (n must be 9246; standard deviations > 0). */
+lbm_status lbm_mlp_params(lbm_mlp* m, float* theta, size_t n);
+lbm_status lbm_mlp_set_params(lbm_mlp* m, const float* theta, size_t n);
+/* Outputs Y[n][4] for host features X[n][9] (the inference path). */
+lbm_status lbm_mlp_forward(lbm_mlp* m, const float* X, int64_t n, float* Y);
+/* Gradient of the loss over all n samples with respect to the 9220 trainable
+ * parameters (the training path, one batch), and the loss itself. */
+lbm_status lbm_mlp_gradient(lbm_mlp* m, const float* X, const float* Y, int64_t n, float* grad,
+                            size_t ngrad, float* loss);
+/* Set the normalisation from the data (means and standard deviations), then
+ * train for `epochs` shuffled passes of minibatches of `batch` samples with
+ * Adam at learning rate lr.  loss_first / loss_last: mean loss seen during the
+ * first / last epoch (either may be NULL). */
+lbm_status lbm_mlp_train(lbm_mlp* m, const float* X, const float* Y, int64_t n, int32_t epochs,
+                         int32_t batch, float lr, uint64_t seed, float* loss_first,
+                         float* loss_last);
+/* Release the network; it must not be in use by a context (lbm_set_correction). */
+void lbm_mlp_destroy(lbm_mlp* m);
+const char* lbm_mlp_last_error(const lbm_mlp* m);
+
+/* Use network m (NULL: none) for the context's first-layer correction with
+ * velocity relaxation rate lam: the correction for the next step is computed
+ * from the current state now and after every step.  The context keeps a
+ * reference: m must stay alive and must not be trained while in use.  Needs
+ * ny >= 3; not available for the boxes of an ensemble. */
+lbm_status lbm_set_correction(lbm_ctx* ctx, const lbm_mlp* m, double lam);
+/* The network inputs of the current state, X[nx*nz][9] (n = 9*nx*nz). */
+lbm_status lbm_features(lbm_ctx* ctx, float* X, size_t n);
+/* The layer-0 acceleration the next step will apply, a[nx*nz][2] (x, z
+ * components; n = 2*nx*nz); LBM_ERR_ARG when no correction is in use. */
+lbm_status lbm_correction_field(lbm_ctx* ctx, float* a, size_t n);
+
 /* ---- ensembles of independent boxes ------------------------------------------
  * Many independent domains ("boxes") of uneven sizes and canopy profiles, as in
  * a wind-siting parameter sweep, advanced together.  The paper runs one domain

@@ -93,6 +93,25 @@ def lib():
             fn = getattr(L, name)
             fn.restype = st
             fn.argtypes = args
+        FP = C.POINTER(C.c_float)
+        L.lbm_mlp_create.restype = st
+        L.lbm_mlp_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
+        for name, args in [("lbm_mlp_params", [vp, FP, C.c_size_t]),
+                           ("lbm_mlp_set_params", [vp, FP, C.c_size_t]),
+                           ("lbm_mlp_forward", [vp, FP, C.c_int64, FP]),
+                           ("lbm_mlp_gradient", [vp, FP, FP, C.c_int64, FP, C.c_size_t, FP]),
+                           ("lbm_mlp_train", [vp, FP, FP, C.c_int64, C.c_int32, C.c_int32,
+                                              C.c_float, C.c_uint64, FP, FP]),
+                           ("lbm_set_correction", [vp, vp, C.c_double]),
+                           ("lbm_features", [vp, FP, C.c_size_t]),
+                           ("lbm_correction_field", [vp, FP, C.c_size_t])]:
+            fn = getattr(L, name)
+            fn.restype = st
+            fn.argtypes = args
+        L.lbm_mlp_destroy.restype = None
+        L.lbm_mlp_destroy.argtypes = [vp]
+        L.lbm_mlp_last_error.restype = C.c_char_p
+        L.lbm_mlp_last_error.argtypes = [vp]
         L.lbm_batch_candidates.restype = C.c_int32
         L.lbm_batch_candidates.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _DP,
                                            C.c_int32]
@@ -209,6 +228,124 @@ def lbm_steps_done(ctx):
 
 def lbm_destroy(ctx):
     lib().lbm_destroy(ctx)
+
+
+# ---- learned first-layer correction ---------------------------------------------------
+
+MLP_PARAMS, MLP_WEIGHTS, MLP_IN, MLP_OUT = 9246, 9220, 9, 4
+_FP = C.POINTER(C.c_float)
+
+
+def _fp(a):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_FP)
+
+
+def _mlp_check(status, m, what):
+    if status != LBM_OK:
+        msg = lib().lbm_mlp_last_error(m).decode() if m else ""
+        base = lib().lbm_status_string(status).decode()
+        raise LbmError(status, f"{what}: {base}{(' - ' + msg) if msg else ''}")
+
+
+def lbm_mlp_create(seed, stream_ptr=0):
+    m = C.c_void_p()
+    _mlp_check(lib().lbm_mlp_create(seed, C.c_void_p(stream_ptr or None), C.byref(m)), None,
+               "lbm_mlp_create")
+    return m
+
+
+def lbm_mlp_params(m):
+    th = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _mlp_check(lib().lbm_mlp_params(m, _fp(th), th.size), m, "lbm_mlp_params")
+    return th
+
+
+def lbm_mlp_set_params(m, theta):
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    _mlp_check(lib().lbm_mlp_set_params(m, _fp(th), th.size), m, "lbm_mlp_set_params")
+
+
+def lbm_mlp_forward(m, X):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+    Y = np.zeros((X.shape[0], MLP_OUT), dtype=np.float32)
+    _mlp_check(lib().lbm_mlp_forward(m, _fp(X), X.shape[0], _fp(Y)), m, "lbm_mlp_forward")
+    return Y
+
+
+def lbm_mlp_gradient(m, X, Y):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+    Y = np.ascontiguousarray(Y, dtype=np.float32).reshape(-1, MLP_OUT)
+    g = np.zeros(MLP_WEIGHTS, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _mlp_check(lib().lbm_mlp_gradient(m, _fp(X), _fp(Y), X.shape[0], _fp(g), g.size, _fp(loss)),
+               m, "lbm_mlp_gradient")
+    return g, float(loss[0])
+
+
+def lbm_mlp_train(m, X, Y, epochs, batch, lr, seed=1):
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+    Y = np.ascontiguousarray(Y, dtype=np.float32).reshape(-1, MLP_OUT)
+    l0, l1 = np.zeros(1, dtype=np.float32), np.zeros(1, dtype=np.float32)
+    _mlp_check(lib().lbm_mlp_train(m, _fp(X), _fp(Y), X.shape[0], epochs, batch, lr, seed,
+                                   _fp(l0), _fp(l1)), m, "lbm_mlp_train")
+    return float(l0[0]), float(l1[0])
+
+
+def lbm_mlp_destroy(m):
+    lib().lbm_mlp_destroy(m)
+
+
+def lbm_set_correction(ctx, m, lam):
+    _check(lib().lbm_set_correction(ctx, m, float(lam)), ctx, "lbm_set_correction")
+
+
+def lbm_features(ctx, n_columns):
+    X = np.zeros((n_columns, MLP_IN), dtype=np.float32)
+    _check(lib().lbm_features(ctx, _fp(X), X.size), ctx, "lbm_features")
+    return X
+
+
+def lbm_correction_field(ctx, n_columns):
+    a = np.zeros((n_columns, 2), dtype=np.float32)
+    _check(lib().lbm_correction_field(ctx, _fp(a), a.size), ctx, "lbm_correction_field")
+    return a
+
+
+class CorrectionNet:
+    """The learned first-layer correction network (see include/lbm.h)."""
+
+    def __init__(self, seed=1, stream=None):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.m = lbm_mlp_create(seed, self.stream.cuda_stream)
+
+    def params(self):
+        return lbm_mlp_params(self.m)
+
+    def set_params(self, theta):
+        lbm_mlp_set_params(self.m, theta)
+
+    def forward(self, X):
+        return lbm_mlp_forward(self.m, X)
+
+    def gradient(self, X, Y):
+        return lbm_mlp_gradient(self.m, X, Y)
+
+    def train(self, X, Y, epochs=20, batch=1024, lr=1e-3, seed=1):
+        return lbm_mlp_train(self.m, X, Y, epochs, batch, lr, seed)
+
+    def close(self):
+        if getattr(self, "m", None) is not None:
+            lbm_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- ensembles ----------------------------------------------------------------------
@@ -365,6 +502,18 @@ class Domain:
 
     def steps_done(self):
         return lbm_steps_done(self.ctx)
+
+    def features(self):
+        """Correction-network inputs of the current state, (nz*nx, 9)."""
+        return lbm_features(self.ctx, self.case.nx * self.case.nz)
+
+    def set_correction(self, net, lam=0.0):
+        """Apply `net` (a CorrectionNet, or None) as the first-layer correction."""
+        self._net = net
+        lbm_set_correction(self.ctx, net.m if net is not None else None, lam)
+
+    def correction_field(self):
+        return lbm_correction_field(self.ctx, self.case.nx * self.case.nz)
 
 
 def _case_inputs(case):

@@ -19,6 +19,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
+#include "lbm_mlp.cuh"
 
 using namespace lbm;
 
@@ -53,8 +54,8 @@ Shape shape_of(const lbm_grid& gr, int storage, int xt = 0) {
 }
 
 struct Layout {
-  size_t f_bytes, stats_off, state_off, ubpart_off, kdrag_off, feqin_off, uprof_off, mass_off,
-      total;
+  size_t f_bytes, stats_off, state_off, ubpart_off, kdrag_off, lad_off, feqin_off, uprof_off,
+      mass_off, accel_off, total;
 };
 
 Layout layout_of(const lbm_grid& g, int storage, int nbins, int xt = 0) {
@@ -66,9 +67,11 @@ Layout layout_of(const lbm_grid& g, int storage, int nbins, int xt = 0) {
   L.state_off = off;  off += align_up(sizeof(DevState), kAlign);
   L.ubpart_off = off; off += align_up(sizeof(double) * 2 * MAX_BLOCKS, kAlign);
   L.kdrag_off = off;  off += align_up(sizeof(float) * g.ny, kAlign);
+  L.lad_off = off;    off += align_up(sizeof(float) * g.ny, kAlign);
   L.feqin_off = off;  off += align_up(sizeof(float) * NQ * g.ny, kAlign);
   L.uprof_off = off;  off += align_up(sizeof(double) * g.ny, kAlign);
   L.mass_off = off;   off += align_up(sizeof(double) * (kMassBlocks + 1), kAlign);
+  L.accel_off = off;  off += align_up(sizeof(float2) * g.nx * g.nz, kAlign);
   L.total = off;
   return L;
 }
@@ -117,12 +120,17 @@ struct lbm_ctx {
   lbm_status status = LBM_OK;
   std::string err;
   lbm_batch* batch = nullptr;  // owning ensemble, if this domain is one of its boxes
+  const lbm_mlp* mlp = nullptr;  // learned first-layer correction in use, if any
+  float lam = 0.f;               // its velocity relaxation rate
+  float* feat_buf = nullptr;     // staging buffer of lbm_features
 
   void* fbuf(int k) const { return ws + (size_t)k * L.f_bytes; }
   double* stats() const { return reinterpret_cast<double*>(ws + L.stats_off); }
   DevState* state() const { return reinterpret_cast<DevState*>(ws + L.state_off); }
   double* ub_part() const { return reinterpret_cast<double*>(ws + L.ubpart_off); }
   float* kdrag() const { return reinterpret_cast<float*>(ws + L.kdrag_off); }
+  float* lad_dev() const { return reinterpret_cast<float*>(ws + L.lad_off); }
+  float2* accel() const { return reinterpret_cast<float2*>(ws + L.accel_off); }
   float* feq_in() const { return reinterpret_cast<float*>(ws + L.feqin_off); }
   double* uprof_dev() const { return reinterpret_cast<double*>(ws + L.uprof_off); }
   double* mass_buf() const { return reinterpret_cast<double*>(ws + L.mass_off); }
@@ -131,6 +139,23 @@ struct lbm_ctx {
     return (((long long)y * grid.nz + z) * sh.nxc + x / sh.xt) * sh.row + (long long)q * sh.xtp +
            sh.g + x % sh.xt;
   }
+};
+
+// A correction network: parameters and training state on the device.
+struct lbm_mlp {
+  float* theta = nullptr;       // [MLP_NP] weights, biases and normalisation (FP32 master copy)
+  float* adam_m = nullptr;      // [MLP_NW] Adam first moments
+  float* adam_v = nullptr;      // [MLP_NW] Adam second moments
+  float* grad = nullptr;        // [MLP_NW] gradient of the last batch
+  float* sse = nullptr;         // sum of squared errors of the last pass
+  float* scratch = nullptr;     // training activations and deltas
+  long long scratch_rows = 0;
+  float* data = nullptr;        // training set on the device (X then Y)
+  long long data_rows = 0;
+  int* perm = nullptr;          // sample order of an epoch
+  long long adam_t = 0;         // Adam steps taken
+  cudaStream_t stream = nullptr;
+  std::string err;
 };
 
 namespace {
@@ -189,6 +214,8 @@ StepParams make_params(const lbm_ctx* c) {
   p.canopy_x0 = c->forcing.x_canopy_begin;
   p.canopy_x1 = c->forcing.x_canopy_end;
   p.kdrag = c->lad.empty() ? nullptr : c->kdrag();
+  p.lad = c->lad.empty() ? nullptr : c->lad_dev();
+  p.accel0 = c->mlp ? c->accel() : nullptr;
   p.feq_in = c->feq_in();
   double ft[NQ];
   feq_shift(c->forcing.u_top, ft);
@@ -292,6 +319,19 @@ void launch_mass(const lbm_ctx* c) {
 template <int XT, int S>
 void launch_macro(const lbm_ctx* c, const StepParams& p, float* out) {
   macro_kernel<XT, S><<<c->sm_count * 8, 256, 0, c->stream>>>(p, out);
+}
+
+// The learned correction over all first-cell columns: with th, the layer-0
+// acceleration for the next step; with th == nullptr, the raw features into X.
+void launch_correction(const lbm_ctx* c, const float* th, float* X) {
+  const StepParams p = make_params(c);
+  const long long cols = (long long)c->grid.nx * c->grid.nz;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((cols + 127) / 128,
+                                                                     (long long)c->sm_count * 8));
+  dispatch(c, [&](auto xt, auto s) {
+    correction_kernel<decltype(xt)::value, decltype(s)::value>
+        <<<blocks, 128, 0, c->stream>>>(p, th, c->lam, c->accel(), X);
+  });
 }
 
 lbm_status check_device(lbm_ctx* c) {
@@ -403,9 +443,10 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
   if (cudaGetLastError() != cudaSuccess) return bail(LBM_ERR_CUDA);
 
   // boundary tables and inputs
-  std::vector<float> kd(grid->ny, 0.f), fin((size_t)NQ * grid->ny, 0.f);
+  std::vector<float> kd(grid->ny, 0.f), la(grid->ny, 0.f), fin((size_t)NQ * grid->ny, 0.f);
   for (int y = 0; y < grid->ny; y++) {
     if (!c->lad.empty()) kd[y] = (float)(forcing->cd * c->lad[y]);
+    if (!c->lad.empty()) la[y] = (float)c->lad[y];
     const double u[3] = {c->uprof[y], 0.0, 0.0};
     double fs[NQ];
     feq_shift(u, fs);
@@ -413,6 +454,8 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
   }
   if (cudaMemsetAsync(c->ws, 0, c->L.total, c->stream) != cudaSuccess ||
       cudaMemcpyAsync(c->kdrag(), kd.data(), sizeof(float) * grid->ny, cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->lad_dev(), la.data(), sizeof(float) * grid->ny, cudaMemcpyHostToDevice,
                       c->stream) != cudaSuccess ||
       cudaMemcpyAsync(c->feq_in(), fin.data(), sizeof(float) * fin.size(),
                       cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
@@ -457,6 +500,11 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     c->cur = 1 - c->cur;
     c->steps++;
     if (c->stats_on) c->stats_samples++;
+    if (c->mlp) {
+      // the next step's layer-0 acceleration from the new state
+      launch_correction(c, c->mlp->theta, nullptr);
+      CK(c, cudaGetLastError());
+    }
   }
   return LBM_OK;
 }
@@ -749,6 +797,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (!c || c->batch) return;  // boxes of an ensemble go with lbm_batch_destroy
   cudaStreamSynchronize(c->stream);
   if (c->macro_buf) cudaFree(c->macro_buf);
+  if (c->feat_buf) cudaFree(c->feat_buf);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   delete c;
 }
@@ -1159,5 +1208,313 @@ void lbm_batch_destroy(lbm_batch* b) {
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---- learned first-layer correction -------------------------------------------------
+namespace {
+
+lbm_status mlp_fail(lbm_mlp* m, lbm_status s, const std::string& what) {
+  cudaGetLastError();
+  m->err = what;
+  return s;
+}
+
+// Glorot-uniform weights from SplitMix64 (counter-based), zero biases, unit normalisation.
+void mlp_init_host(std::vector<float>& th, uint64_t seed) {
+  th.assign(MLP_NP, 0.f);
+  const int offs[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4};
+  const int fan_in[4] = {MLP_IN, MLP_H, MLP_H, MLP_H}, fan_out[4] = {MLP_H, MLP_H, MLP_H, MLP_OUT};
+  uint64_t k = 0;
+  for (int l = 0; l < 4; l++) {
+    const double r = std::sqrt(6.0 / (fan_in[l] + fan_out[l]));
+    for (int e = 0; e < fan_in[l] * fan_out[l]; e++) {
+      uint64_t z = seed + (++k) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;  // [-1, 1)
+      th[offs[l] + e] = (float)(r * u);
+    }
+  }
+  for (int i = 0; i < MLP_IN; i++) th[OFF_XS + i] = 1.f;
+  for (int i = 0; i < MLP_OUT; i++) th[OFF_YS + i] = 1.f;
+}
+
+// Training buffers for `rows` samples: H0 (9), H1..H3 (64), D1..D3 (64), D4 (4) per row.
+constexpr long long kTrainFloatsPerRow = 9 + 3 * 64 + 3 * 64 + 4;
+
+lbm_status mlp_scratch(lbm_mlp* m, long long rows) {
+  if (rows <= m->scratch_rows) return LBM_OK;
+  if (m->scratch) cudaFree(m->scratch);
+  m->scratch = nullptr;
+  m->scratch_rows = 0;
+  if (cudaMalloc(&m->scratch, sizeof(float) * kTrainFloatsPerRow * rows) != cudaSuccess)
+    return mlp_fail(m, LBM_ERR_OOM, "lbm_mlp: cudaMalloc of the training buffers failed");
+  m->scratch_rows = rows;
+  return LBM_OK;
+}
+
+// Forward, backward and weight gradients of `n` samples (rows idx[0..n) of X,
+// Y, or the first n rows when idx is null) into m->grad; the loss is the mean
+// over n_total samples and 4 outputs.
+void mlp_pass(lbm_mlp* m, const float* X, const float* Y, const int* idx, int n, int n_total) {
+  float* H0 = m->scratch;
+  float* H1 = H0 + 9ll * n;
+  float* H2 = H1 + 64ll * n;
+  float* H3 = H2 + 64ll * n;
+  float* D1 = H3 + 64ll * n;
+  float* D2 = D1 + 64ll * n;
+  float* D3 = D2 + 64ll * n;
+  float* D4 = D3 + 64ll * n;
+  const int blocks = (n + 127) / 128;
+  const float scale = 2.0f / (4.0f * (float)n_total);
+  mlp_train_fwd<<<blocks, 128, 0, m->stream>>>(m->theta, X, Y, idx, n, scale, H0, H1, H2, H3, D4,
+                                               m->sse);
+  mlp_train_bwd<<<blocks, 128, 0, m->stream>>>(m->theta, n, H1, H2, H3, D4, D1, D2, D3);
+  cudaMemsetAsync(m->grad, 0, sizeof(float) * MLP_NW, m->stream);
+  const int rows_per_slice = 256;
+  const int slices = (n + rows_per_slice - 1) / rows_per_slice;
+  const float* Ds[4] = {D1, D2, D3, D4};
+  const float* Hs[4] = {H0, H1, H2, H3};
+  const int nouts[4] = {64, 64, 64, 4}, nins[4] = {9, 64, 64, 64};
+  const int offw[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4}, offb[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4};
+  for (int l = 0; l < 4; l++) {
+    dim3 grid(slices, (nouts[l] + 3) / 4);
+    mlp_train_wgrad<<<grid, 256, 0, m->stream>>>(Ds[l], nouts[l], Hs[l], nins[l], n,
+                                                 rows_per_slice, m->grad + offw[l], m->grad + offb[l]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_mlp_create(uint64_t seed, void* cuda_stream, lbm_mlp** out) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  lbm_mlp* m = new (std::nothrow) lbm_mlp();
+  if (!m) return LBM_ERR_OOM;
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<float> th;
+  mlp_init_host(th, seed);
+  bool ok = cudaMalloc(&m->theta, sizeof(float) * MLP_NP) == cudaSuccess &&
+            cudaMalloc(&m->adam_m, sizeof(float) * MLP_NW) == cudaSuccess &&
+            cudaMalloc(&m->adam_v, sizeof(float) * MLP_NW) == cudaSuccess &&
+            cudaMalloc(&m->grad, sizeof(float) * MLP_NW) == cudaSuccess &&
+            cudaMalloc(&m->sse, sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMemcpy(m->theta, th.data(), sizeof(float) * MLP_NP, cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lbm_mlp_destroy(m);
+    return LBM_ERR_OOM;
+  }
+  *out = m;
+  return LBM_OK;
+}
+
+lbm_status lbm_mlp_params(lbm_mlp* m, float* theta, size_t n) {
+  if (!m || !theta || n != (size_t)MLP_NP) return LBM_ERR_ARG;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess ||
+      cudaMemcpy(theta, m->theta, sizeof(float) * MLP_NP, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_params: copy failed");
+  return LBM_OK;
+}
+
+lbm_status lbm_mlp_set_params(lbm_mlp* m, const float* theta, size_t n) {
+  if (!m || !theta || n != (size_t)MLP_NP) return LBM_ERR_ARG;
+  for (int i = 0; i < MLP_IN; i++)
+    if (!(theta[OFF_XS + i] > 0.f)) return LBM_ERR_ARG;
+  for (int i = 0; i < MLP_OUT; i++)
+    if (!(theta[OFF_YS + i] > 0.f)) return LBM_ERR_ARG;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess ||
+      cudaMemcpy(m->theta, theta, sizeof(float) * MLP_NP, cudaMemcpyHostToDevice) != cudaSuccess)
+    return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_set_params: copy failed");
+  m->adam_t = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_mlp_forward(lbm_mlp* m, const float* X, int64_t n, float* Y) {
+  if (!m || !X || !Y || n < 0 || n > (1ll << 30)) return LBM_ERR_ARG;
+  if (n == 0) return LBM_OK;
+  float* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(float) * (MLP_IN + MLP_OUT) * n) != cudaSuccess)
+    return mlp_fail(m, LBM_ERR_OOM, "lbm_mlp_forward: cudaMalloc failed");
+  float* dY = buf + MLP_IN * n;
+  cudaMemcpyAsync(buf, X, sizeof(float) * MLP_IN * n, cudaMemcpyHostToDevice, m->stream);
+  const long long tiles = (n + 15) / 16;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((tiles + 3) / 4, 4096));
+  mlp_infer_kernel<<<blocks, 128, 0, m->stream>>>(m->theta, buf, n, dY);
+  cudaMemcpyAsync(Y, dY, sizeof(float) * MLP_OUT * n, cudaMemcpyDeviceToHost, m->stream);
+  const cudaError_t e = cudaStreamSynchronize(m->stream);
+  cudaFree(buf);
+  if (e != cudaSuccess) return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_forward: kernel failed");
+  return LBM_OK;
+}
+
+lbm_status lbm_mlp_gradient(lbm_mlp* m, const float* X, const float* Y, int64_t n, float* grad,
+                            size_t ngrad, float* loss) {
+  if (!m || !X || !Y || !grad || ngrad != (size_t)MLP_NW || n < 1 || n > (1 << 22))
+    return LBM_ERR_ARG;
+  lbm_status s = mlp_scratch(m, n);
+  if (s != LBM_OK) return s;
+  float* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(float) * (MLP_IN + MLP_OUT) * n) != cudaSuccess)
+    return mlp_fail(m, LBM_ERR_OOM, "lbm_mlp_gradient: cudaMalloc failed");
+  cudaMemcpyAsync(buf, X, sizeof(float) * MLP_IN * n, cudaMemcpyHostToDevice, m->stream);
+  cudaMemcpyAsync(buf + MLP_IN * n, Y, sizeof(float) * MLP_OUT * n, cudaMemcpyHostToDevice,
+                  m->stream);
+  cudaMemsetAsync(m->sse, 0, sizeof(float), m->stream);
+  mlp_pass(m, buf, buf + MLP_IN * n, nullptr, (int)n, (int)n);
+  float sse = 0.f;
+  cudaMemcpyAsync(grad, m->grad, sizeof(float) * MLP_NW, cudaMemcpyDeviceToHost, m->stream);
+  cudaMemcpyAsync(&sse, m->sse, sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+  const cudaError_t e = cudaStreamSynchronize(m->stream);
+  cudaFree(buf);
+  if (e != cudaSuccess) return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_gradient: kernel failed");
+  if (loss) *loss = sse / (4.0f * (float)n);
+  return LBM_OK;
+}
+
+lbm_status lbm_mlp_train(lbm_mlp* m, const float* X, const float* Y, int64_t n, int32_t epochs,
+                         int32_t batch, float lr, uint64_t seed, float* loss_first,
+                         float* loss_last) {
+  if (!m || !X || !Y || n < 1 || n > (1 << 26) || epochs < 1 || batch < 1 || !(lr > 0.f))
+    return LBM_ERR_ARG;
+  batch = (int32_t)std::min<int64_t>(batch, n);
+  // normalisation from the training set (mean and standard deviation; a
+  // constant input or target keeps unit scale)
+  std::vector<float> th(MLP_NP);
+  if (cudaMemcpy(th.data(), m->theta, sizeof(float) * MLP_NP, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_train: copy failed");
+  for (int pass = 0; pass < 2; pass++) {
+    const float* D = pass == 0 ? X : Y;
+    const int w = pass == 0 ? MLP_IN : MLP_OUT;
+    for (int k = 0; k < w; k++) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int64_t r = 0; r < n; r++) {
+        const double v = D[r * w + k];
+        s1 += v;
+        s2 += v * v;
+      }
+      const double mean = s1 / n, var = std::max(0.0, s2 / n - mean * mean);
+      const double sd = var > 1e-30 * std::max(1.0, mean * mean) ? std::sqrt(var) : 1.0;
+      th[(pass == 0 ? OFF_XM : OFF_YM) + k] = (float)mean;
+      th[(pass == 0 ? OFF_XS : OFF_YS) + k] = (float)sd;
+    }
+  }
+  if (n > m->data_rows) {
+    if (m->data) cudaFree(m->data);
+    if (m->perm) cudaFree(m->perm);
+    m->data = nullptr;
+    m->perm = nullptr;
+    m->data_rows = 0;
+    if (cudaMalloc(&m->data, sizeof(float) * (MLP_IN + MLP_OUT) * n) != cudaSuccess ||
+        cudaMalloc(&m->perm, sizeof(int) * n) != cudaSuccess)
+      return mlp_fail(m, LBM_ERR_OOM, "lbm_mlp_train: cudaMalloc of the training set failed");
+    m->data_rows = n;
+  }
+  lbm_status s = mlp_scratch(m, batch);
+  if (s != LBM_OK) return s;
+  float* dX = m->data;
+  float* dY = m->data + MLP_IN * n;
+  bool ok = cudaMemcpy(m->theta, th.data(), sizeof(float) * MLP_NP, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(dX, X, sizeof(float) * MLP_IN * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(dY, Y, sizeof(float) * MLP_OUT * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemset(m->adam_m, 0, sizeof(float) * MLP_NW) == cudaSuccess &&
+            cudaMemset(m->adam_v, 0, sizeof(float) * MLP_NW) == cudaSuccess;
+  if (!ok) return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_train: upload failed");
+  m->adam_t = 0;
+  std::vector<int> perm(n);
+  for (int64_t r = 0; r < n; r++) perm[r] = (int)r;
+  uint64_t draw = 0;
+  for (int e = 0; e < epochs; e++) {
+    // Fisher-Yates shuffle with SplitMix64 draws
+    for (int64_t r = n - 1; r > 0; r--) {
+      uint64_t z = seed + (++draw) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      std::swap(perm[r], perm[z % (uint64_t)(r + 1)]);
+    }
+    cudaMemcpyAsync(m->perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream);
+    cudaMemsetAsync(m->sse, 0, sizeof(float), m->stream);
+    for (int64_t b0 = 0; b0 < n; b0 += batch) {
+      const int nb = (int)std::min<int64_t>(batch, n - b0);
+      mlp_pass(m, dX, dY, m->perm + b0, nb, nb);
+      m->adam_t++;
+      const double c1 = 1.0 / (1.0 - std::pow(0.9, (double)m->adam_t));
+      const double c2 = 1.0 / (1.0 - std::pow(0.999, (double)m->adam_t));
+      mlp_adam<<<(MLP_NW + 255) / 256, 256, 0, m->stream>>>(m->theta, m->grad, m->adam_m, m->adam_v,
+                                                          MLP_NW, lr, (float)c1, (float)c2);
+    }
+    float sse = 0.f;
+    cudaMemcpyAsync(&sse, m->sse, sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess)
+      return mlp_fail(m, LBM_ERR_CUDA, "lbm_mlp_train: kernel failed");
+    const float l = sse / (4.0f * (float)n);  // mean over the epoch's batches (pre-update losses)
+    if (e == 0 && loss_first) *loss_first = l;
+    if (loss_last) *loss_last = l;
+  }
+  return LBM_OK;
+}
+
+void lbm_mlp_destroy(lbm_mlp* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  for (float* p : {m->theta, m->adam_m, m->adam_v, m->grad, m->sse, m->scratch, m->data})
+    if (p) cudaFree(p);
+  if (m->perm) cudaFree(m->perm);
+  delete m;
+}
+
+const char* lbm_mlp_last_error(const lbm_mlp* m) { return m ? m->err.c_str() : "no network"; }
+
+lbm_status lbm_set_correction(lbm_ctx* c, const lbm_mlp* m, double lam) {
+  READY(c);
+  if (c->batch) return arg_error(c, "lbm_set_correction: not available for ensemble boxes");
+  if (m && c->grid.ny < 3) return arg_error(c, "lbm_set_correction: needs ny >= 3");
+  if (!std::isfinite(lam)) return arg_error(c, "lbm_set_correction: lam not finite");
+  c->mlp = m;
+  c->lam = (float)lam;
+  if (m) {
+    CK(c, cudaStreamSynchronize(m->stream));  // the network's parameters are ready
+    launch_correction(c, m->theta, nullptr);
+    CK(c, cudaGetLastError());
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_features(lbm_ctx* c, float* X, size_t n) {
+  READY(c);
+  const size_t cols = (size_t)c->grid.nx * c->grid.nz;
+  if (!X || n != cols * MLP_IN) return arg_error(c, "lbm_features: wrong size");
+  if (c->grid.ny < 3) return arg_error(c, "lbm_features: needs ny >= 3");
+  if (!c->feat_buf) {
+    if (cudaMalloc(&c->feat_buf, sizeof(float) * cols * MLP_IN) != cudaSuccess) {
+      cudaGetLastError();
+      c->feat_buf = nullptr;
+      return fail(c, LBM_ERR_OOM, "lbm_features: cudaMalloc of the feature buffer failed");
+    }
+  }
+  launch_correction(c, nullptr, c->feat_buf);
+  CK(c, cudaGetLastError());
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  CK(c, cudaMemcpy(X, c->feat_buf, sizeof(float) * cols * MLP_IN, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
+lbm_status lbm_correction_field(lbm_ctx* c, float* a, size_t n) {
+  READY(c);
+  const size_t cols = (size_t)c->grid.nx * c->grid.nz;
+  if (!a || n != 2 * cols) return arg_error(c, "lbm_correction_field: wrong size");
+  if (!c->mlp) return arg_error(c, "lbm_correction_field: no correction in use");
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  CK(c, cudaMemcpy(a, c->accel(), sizeof(float) * 2 * cols, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
 
 }  // extern "C"

@@ -116,6 +116,7 @@ struct StepParams {
   int slot_read, slot_write, nprev;  // nprev: blocks of the previous launch
   int canopy_x0, canopy_x1;
   const float* kdrag;       // ny values C_D a(y), or nullptr
+  const float* lad;         // ny values a(y), or nullptr (inputs of the learned correction)
   const float* feq_in;      // [ny][19] shifted f_eq(1, u_in(y)) for the inflow column
   float feq_top[NQ];        // shifted f_eq(1, u_top) (equilibrium top)
   // tiling: tile = (y, z-group, x-chunk), block = (XT, ry) threads
@@ -126,6 +127,9 @@ struct StepParams {
   double* stats;            // [9][nbins][ny] FP64 sums
   int nbins;
   DevState* state;
+  // learned first-layer correction: extra (x, z) acceleration of the cells at
+  // y = 0, per column [z][x], or nullptr
+  const float2* accel0;
 };
 
 // element index of population q at cell (x, y, z)
@@ -640,7 +644,12 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
             if (cy(i) == -1) f[i] = p.top == 1 ? Store<S>::to_float(sm[i * St::SROW]) : p.feq_top[i];
         }
       }
-      m = moments(f, gx, gy, gz, drag_factor(p, x, y));
+      if (p.accel0 != nullptr && y == 0) {
+        const float2 a = p.accel0[(long long)z * p.nx + x];
+        m = moments(f, gx + a.x, gy, gz + a.y, drag_factor(p, x, y));
+      } else {
+        m = moments(f, gx, gy, gz, drag_factor(p, x, y));
+      }
     }
     // release the stage: the moments consumed every staged value of this warp
     __syncwarp();
@@ -851,12 +860,56 @@ __global__ void mass_final_kernel(const double* partial, int n, double base, dou
 
 // ---- macroscopic fields of the next step (pull + moments only) ------------------------
 // Direct loads with the same boundary rules as the step (not performance critical).
+// The 19 (shifted) populations cell (x, y, z) streams in for the next step,
+// gathered one by one with the step's boundary rules (readouts, not the step).
+template <int XT, int S>
+__device__ __forceinline__ void gather_cell(const StepParams& p, int x, int y, int z, float* f) {
+  using T = typename Store<S>::T;
+  const T* src = static_cast<const T*>(p.src);
+#pragma unroll
+  for (int i = 0; i < NQ; i++) {
+    int q, ys, zs;
+    const int kind = row_source(p, i, cy(i), cz(i), y, z, q, ys, zs);
+    if (kind == SRC_CONST) {
+      f[i] = p.feq_top[i];
+    } else if (kind == SRC_OWN_X) {
+      f[i] = Store<S>::ld(src + pop_index<XT, S>(p, q, x, ys, zs));
+    } else {
+      const int xs = source_x(p, x, cx(i));
+      f[i] = xs < 0 ? p.feq_in[ys * NQ + q] : Store<S>::ld(src + pop_index<XT, S>(p, q, xs, ys, zs));
+    }
+  }
+}
+
+// Strain-rate magnitude |S| = sqrt(2 S:S) of a cell from its non-equilibrium
+// momentum flux (Eq. tensor) through Pi_neq = -2 rho c_s^2 tau_total S, with
+// tau_total from the Smagorinsky closure as in the collision.
+__device__ __forceinline__ float strain_rate(const float* f, const Macro& m, float tau0, float c18) {
+  const float ux = m.ux, uy = m.uy, uz = m.uz;
+  const float base = m.drho - 1.5f * m.rho * (ux * ux + uy * uy + uz * uz);
+  const float r45 = 4.5f * m.rho;
+  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    const float ei = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const float npair = (f[i] + f[i + 1]) - 2.0f * wgt(i) * (base + r45 * ei * ei);
+    if (cx(i) != 0) pxx += npair;
+    if (cy(i) != 0) pyy += npair;
+    if (cz(i) != 0) pzz += npair;
+    pxy += (float)(cx(i) * cy(i)) * npair;
+    pxz += (float)(cx(i) * cz(i)) * npair;
+    pyz += (float)(cy(i) * cz(i)) * npair;
+  }
+  const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
+  const float q = sqrtf(q2);
+  const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * q / m.rho));
+  return 2.1213203435596424f * q / (m.rho * tau);  // sqrt(2) / (2 c_s^2) = 3 / sqrt(2)
+}
+
 template <int XT, int S, class OutT = float>
 __global__ void macro_kernel(StepParams p, OutT* out) {
-  using T = typename Store<S>::T;
   const long long n = (long long)p.nx * p.ny * p.nz;
   const float gx = controlled_gx(p, threadIdx.x & 31);  // blockDim.x is a multiple of 32
-  const T* src = static_cast<const T*>(p.src);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(c % p.nx);
@@ -864,19 +917,7 @@ __global__ void macro_kernel(StepParams p, OutT* out) {
     const int y = (int)(r % p.ny);
     const int z = (int)(r / p.ny);
     float f[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; i++) {
-      int q, ys, zs;
-      const int kind = row_source(p, i, cy(i), cz(i), y, z, q, ys, zs);
-      if (kind == SRC_CONST) {
-        f[i] = p.feq_top[i];
-      } else if (kind == SRC_OWN_X) {
-        f[i] = Store<S>::ld(src + pop_index<XT, S>(p, q, x, ys, zs));
-      } else {
-        const int xs = source_x(p, x, cx(i));
-        f[i] = xs < 0 ? p.feq_in[ys * NQ + q] : Store<S>::ld(src + pop_index<XT, S>(p, q, xs, ys, zs));
-      }
-    }
+    gather_cell<XT, S>(p, x, y, z, f);
     const Macro m = moments(f, gx, p.g[1], p.g[2], drag_factor(p, x, y));
     out[c] = m.rho;
     out[n + c] = m.ux;

@@ -33,7 +33,8 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
     for n in declared:
         assert hasattr(P.lib(), n)
-        assert hasattr(P, n) or n in ("lbm_last_error", "lbm_status_string", "lbm_batch_last_error")
+        assert hasattr(P, n) or n in ("lbm_last_error", "lbm_status_string", "lbm_batch_last_error",
+                                      "lbm_mlp_last_error")
 
 
 def _grid(nx=64, ny=32, nz=16, bc=(0, 0, 1, 2, 0, 0)):
