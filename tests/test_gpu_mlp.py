@@ -124,3 +124,54 @@ def test_corrected_steps_match_oracle_given_the_same_field():
     d.step(3)
     o.step(3)
     assert np.linalg.norm(d.get_f() - o.get_f()) / np.linalg.norm(o.get_f()) < 1e-6
+
+
+def test_corrected_run_statistics_match_oracle_within_2_percent():
+    """The learned form against the FP64 oracle running the same correction
+    (its own features, the network in FP64 with the same BF16 weights), over a
+    statistics window: mean-velocity profiles within 2 %."""
+    th = random_theta(12, scale=0.1)
+    th[M.N_WEIGHTS + 18:M.N_WEIGHTS + 22] = 0.0
+    th[M.N_WEIGHTS + 22:] = 2e-4
+    net = P.CorrectionNet(seed=13)
+    net.set_params(th)
+    tho = as_bf16_weights(th)
+    d, o = P.Domain(CASE), oracle.Oracle(CASE)
+    d.set_correction(net, lam=0.01)
+    d.stats_reset(True)
+    o.stats_reset(True)
+    for k in range(300):
+        o.set_layer0_accel(M.correction_accel(tho, o.features(), 0.01).reshape(CASE.nz, CASE.nx, 2))
+        o.step(1)
+    d.step(300)
+    sd, _ = d.stats()
+    so, _ = o.stats()
+    err = np.abs(sd[:3] - so[:3]).max() / np.abs(so[0]).max()
+    print(f"corrected run: mean-velocity profile error = {err:.2e} of max <u>")
+    assert err < 0.02
+
+
+def test_trained_correction_gains_over_the_plain_coarse_run():
+    """Gain test: a canopy boundary layer (64 x 32 x 32, h = 6, a = 0.25,
+    C_D = 0.15, inflow/outflow) run plain on the coarse grid and on the 2x finer
+    grid; the network is trained on the coarse run's features against the
+    coarsened fine run's first-cell deficits; the corrected coarse run's mean
+    streamwise velocity must be closer to the coarsened fine profile than the
+    plain coarse run's, in the first cell and over the canopy layer."""
+    from paper_2206_15454_b300 import learned as L
+
+    case = W.canopy_abl(64, 32, 32, h=6.0, a=0.25, cd=0.15, canopy_x0=16, xbin=1)
+    spin, avg = 2000, 2000
+    ref = L.reference_runs(case, spin, avg, sample_every=20)
+    net, l0, l1 = L.train_correction(ref, epochs=30)
+    plain, corr = L.corrected_run(case, net, 0.01, spin, avg)
+    out = {}
+    for rows in (1, 6, 12):
+        out[rows] = (L.profile_error(plain, ref.fine_coarsened, rows),
+                     L.profile_error(corr, ref.fine_coarsened, rows))
+    print("training loss %.3f -> %.3f; " % (l0, l1) + "; ".join(
+        f"rows {r}: plain {a:.4f} corrected {b:.4f}" for r, (a, b) in out.items()))
+    assert l1 < 0.6 * l0
+    assert out[1][1] < 0.8 * out[1][0]   # first cell
+    assert out[6][1] < 0.85 * out[6][0]  # the canopy layer
+    assert out[12][1] < out[12][0]
