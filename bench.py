@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16 storage legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-box ensemble leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile", metavar="NXxNYxNZ", default=None,
                     help="run a few steps of the channel workload at this size and exit "
@@ -188,19 +189,25 @@ def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
     d.sync()
     torch.cuda.synchronize()
     barrier(ws)
+    # the timed region: `steps` launches back to back, events only around them
     t_begin = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
     t_begin.record(stream)
-    for a, b in ev:
-        a.record(stream)
-        d.step(1)
-        b.record(stream)
+    d.step(steps)
     t_end.record(stream)
     torch.cuda.synchronize()
     d.sync()
     total_ms = t_begin.elapsed_time(t_end)
+    barrier(ws)
+    # the step kernel's own duration: events around each launch of a second run
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(min(steps, 200))]
+    for a, b in ev:
+        a.record(stream)
+        d.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    d.sync()
     per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     return d, case, total_ms, per_launch_ms
 
@@ -235,6 +242,52 @@ def time_ensemble(P, W, steps, warmup, hbm):
                                      for c in b.candidates()]}}
     b.close()
     return out
+
+
+def time_learned(P, W, steps, warmup):
+    """The learned first-layer correction: (1) its gain on a 64x32x32 canopy
+    boundary layer (trained on the plain coarse and 2x-fine runs, error of the
+    mean streamwise velocity against the coarsened fine run), (2) throughput
+    of the 1024x256x512 canopy domain (h = 12, a = 0.25, C_D = 0.15,
+    inflow/outflow, FP32) with and without the correction in every step."""
+    import torch
+
+    from paper_2206_15454_b300 import learned as L
+
+    small = W.canopy_abl(64, 32, 32, h=6.0, a=0.25, cd=0.15, canopy_x0=16, xbin=1)
+    ref = L.reference_runs(small, 2000, 2000, sample_every=20)
+    net, l0, l1 = L.train_correction(ref, epochs=30)
+    plain, corr = L.corrected_run(small, net, 0.01, 2000, 2000)
+    gain = {f"rows_{r}": {"plain": round(L.profile_error(plain, ref.fine_coarsened, r), 4),
+                          "corrected": round(L.profile_error(corr, ref.fine_coarsened, r), 4)}
+            for r in (1, 6, 12)}
+
+    case = W.canopy_abl(1024, 256, 512, h=12.0, a=0.25, cd=0.15, canopy_x0=256, xbin=16)
+    d = P.Domain(case, P.LBM_F32)
+    out = {}
+    for label, use in (("plain", False), ("corrected", True)):
+        if use:
+            d.set_correction(net, 0.01)
+        d.step(warmup)
+        d.sync()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(d.stream)
+        d.step(steps)
+        t1.record(d.stream)
+        torch.cuda.synchronize()
+        d.sync()
+        ms = t0.elapsed_time(t1) / steps
+        out[label] = {"value": round(case.cells / ms / 1e3, 1), "unit": "MLUPS", "ms_per_step": ms}
+    d.close()
+    net.close()
+    return {"workload": "canopy ABL 1024x256x512 (h=12, a=0.25, C_D=0.15, inflow/outflow), FP32",
+            "cells": case.cells, "steps": steps, **out,
+            "correction_share_of_step": round(1 - out["plain"]["ms_per_step"] /
+                                              out["corrected"]["ms_per_step"], 4),
+            "gain": {"workload": "canopy ABL 64x32x32 (h=6) vs the same on 128x64x64, "
+                                 "2000 + 2000 steps, lam = 0.01",
+                     "training_loss": [round(l0, 4), round(l1, 4)],
+                     "mean_u_rel_l2_vs_coarsened_fine": gain}}
 
 
 def e2e_run(P, d, steps):
@@ -345,6 +398,8 @@ def run_ours(args):
                          "rel_l2_f_vs_f32_after_100_steps": err}
     if not args.no_ensemble:
         res["ensemble"] = time_ensemble(P, W, min(args.steps, 1000), max(args.warmup, 3), hbm)
+    if not args.no_learned:
+        res["learned"] = time_learned(P, W, min(args.steps, 100), max(min(args.warmup, 10), 3))
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(W.channel_les, args.cpu_seconds)
     if rank == 0:

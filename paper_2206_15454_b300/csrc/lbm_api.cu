@@ -252,11 +252,23 @@ int step_grid(const lbm_ctx* c) {
 
 template <int XT, int S>
 void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
-  const int grid = step_grid(c);
+  // programmatic dependent launch: the blocks of this step may start while the
+  // previous step's last blocks finish; the kernel waits (griddepcontrol.wait)
+  // before it touches memory the previous step wrote or reads
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(step_grid(c));
+  cfg.blockDim = c->block;
+  cfg.dynamicSmemBytes = c->stage_smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (stats)
-    step_kernel<XT, S, true><<<grid, c->block, c->stage_smem, c->stream>>>(p);
+    cudaLaunchKernelEx(&cfg, step_kernel<XT, S, true>, p);
   else
-    step_kernel<XT, S, false><<<grid, c->block, c->stage_smem, c->stream>>>(p);
+    cudaLaunchKernelEx(&cfg, step_kernel<XT, S, false>, p);
 }
 
 // Shared-memory stages: as many tiles in flight as fit beside three blocks

@@ -562,6 +562,12 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 #pragma unroll
     for (int k = 0; k < 9; k++) s_q[k * 256 + tid] = 0.f;
   }
+  // Launched as a programmatic dependent of the previous step: let the next
+  // step's blocks be scheduled as this grid's blocks retire, then wait here
+  // until the previous step has completed and its writes are visible (both
+  // are no-ops for an ordinary launch).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     for (int k = 0; k < p.nstage && k < ntile; k++)
