@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-box ensemble leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--profile", metavar="NXxNYxNZ", default=None,
-                    help="run a few steps of the channel workload at this size and exit "
-                         "(the case the ncu summaries under profiles/ capture)")
+    ap.add_argument("--profile", metavar="NXxNYxNZ|ensemble|learned", default=None,
+                    help="run a few steps of the channel workload at this size (or of the "
+                         "64-box ensemble, or of a 256x64x128 canopy domain with the learned "
+                         "correction) and exit: the cases the ncu summaries under profiles/ "
+                         "capture")
     return ap.parse_args()
 
 
@@ -459,8 +461,25 @@ def run_profile_case(args):
     import paper_2206_15454_b300 as P
     import workloads as W
 
-    nx, ny, nz = (int(v) for v in args.profile.lower().split("x"))
     torch.cuda.set_device(0)
+    if args.profile == "ensemble":
+        b = P.Batch(W.ensemble_boxes(), P.LBM_F16_SHIFTED)
+        b.step(6)
+        b.sync()
+        b.close()
+        print("profile case: 64-box ensemble, FP16-shifted: 6 steps done")
+        return
+    if args.profile == "learned":
+        d = P.Domain(W.canopy_abl(256, 64, 128, h=12.0, a=0.25, cd=0.15, canopy_x0=64, xbin=16))
+        net = P.CorrectionNet(seed=1)
+        d.set_correction(net, 0.01)
+        d.step(6)
+        d.sync()
+        d.close()
+        net.close()
+        print("profile case: canopy 256x64x128 with the learned correction: 6 steps done")
+        return
+    nx, ny, nz = (int(v) for v in args.profile.lower().split("x"))
     d = P.Domain(W.channel_les(nx, ny, nz), P.STORAGE_NAMES[args.storage])
     d.stats_reset(True)
     d.step(6)
