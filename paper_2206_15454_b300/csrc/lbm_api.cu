@@ -26,6 +26,9 @@ using namespace lbm;
 namespace {
 
 constexpr size_t kAlign = 256;
+#ifndef LBM_STATIC_PERCENT
+#define LBM_STATIC_PERCENT 90
+#endif
 constexpr int kMassBlocks = 1024;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -65,7 +68,7 @@ Layout layout_of(const lbm_grid& g, int storage, int nbins, int xt = 0) {
   size_t off = 2 * L.f_bytes;
   L.stats_off = off;  off += align_up(sizeof(double) * 9 * nbins * g.ny, kAlign);
   L.state_off = off;  off += align_up(sizeof(DevState), kAlign);
-  L.ubpart_off = off; off += align_up(sizeof(double) * 2 * MAX_BLOCKS, kAlign);
+  L.ubpart_off = off; off += align_up(sizeof(long long) * 2 * MAX_BLOCKS, kAlign);
   L.kdrag_off = off;  off += align_up(sizeof(float) * g.ny, kAlign);
   L.lad_off = off;    off += align_up(sizeof(float) * g.ny, kAlign);
   L.feqin_off = off;  off += align_up(sizeof(float) * NQ * g.ny, kAlign);
@@ -127,7 +130,7 @@ struct lbm_ctx {
   void* fbuf(int k) const { return ws + (size_t)k * L.f_bytes; }
   double* stats() const { return reinterpret_cast<double*>(ws + L.stats_off); }
   DevState* state() const { return reinterpret_cast<DevState*>(ws + L.state_off); }
-  double* ub_part() const { return reinterpret_cast<double*>(ws + L.ubpart_off); }
+  long long* ub_part() const { return reinterpret_cast<long long*>(ws + L.ubpart_off); }
   float* kdrag() const { return reinterpret_cast<float*>(ws + L.kdrag_off); }
   float* lad_dev() const { return reinterpret_cast<float*>(ws + L.lad_off); }
   float2* accel() const { return reinterpret_cast<float2*>(ws + L.accel_off); }
@@ -189,6 +192,15 @@ void feq_shift(const double u[3], double out[NQ]) {
   }
 }
 
+// Percentage of a step's tiles that blocks take in their fixed runs.
+constexpr long long kStaticPercent = LBM_STATIC_PERCENT;
+
+int step_grid(const lbm_ctx* c) {
+  const long long ntiles = (long long)c->sh.nxc * c->nzg * c->grid.ny;
+  const long long want = (long long)c->sm_count * c->blocks_per_sm;
+  return (int)std::max<long long>(1, std::min<long long>({want, ntiles, (long long)MAX_BLOCKS}));
+}
+
 StepParams make_params(const lbm_ctx* c) {
   StepParams p;
   std::memset(&p, 0, sizeof(p));
@@ -223,6 +235,11 @@ StepParams make_params(const lbm_ctx* c) {
   p.nzg = c->nzg;
   p.ntiles = (long long)c->sh.nxc * c->nzg * g.ny;
   p.nstage = c->nstage;
+  // a share of the tiles in fixed contiguous runs per block, the rest handed
+  // out one by one to whichever block is free (blocks of an SM do not run at
+  // the same speed)
+  p.static_tiles = (int)(p.ntiles * kStaticPercent / 100 / step_grid(c));
+  p.ctr_slot = (int)(c->steps & 1);
   p.stats = c->stats();
   p.nbins = c->nbins;
   p.state = c->state();
@@ -244,11 +261,6 @@ void dispatch(const lbm_ctx* c, Fn&& fn) {
   else by_storage(std::integral_constant<int, 256>());
 }
 
-int step_grid(const lbm_ctx* c) {
-  const long long ntiles = (long long)c->sh.nxc * c->nzg * c->grid.ny;
-  const long long want = (long long)c->sm_count * c->blocks_per_sm;
-  return (int)std::max<long long>(1, std::min<long long>({want, ntiles, (long long)MAX_BLOCKS}));
-}
 
 template <int XT, int S>
 void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
@@ -656,11 +668,12 @@ lbm_status lbm_drive(lbm_ctx* c, double g[3], double* u_bulk) {
   if (s != LBM_OK) return s;
   double ub = 0.0;
   if (c->steps > 0) {
-    std::vector<double> part(c->last_grid);
+    std::vector<long long> part(c->last_grid);
     CK(c, cudaMemcpy(part.data(), c->ub_part() + (size_t)((c->steps + 1) % 2) * MAX_BLOCKS,
-                     sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
-    for (double v : part) ub += v;
-    ub /= (double)c->cells;
+                     sizeof(long long) * part.size(), cudaMemcpyDeviceToHost));
+    long long sum = 0;
+    for (long long v : part) sum += v;
+    ub = (double)sum / 4294967296.0 / (double)c->cells;
   }
   for (int a = 0; a < 3; a++) g[a] = c->forcing.g[a];
   if (c->forcing.u_bulk_target > 0.0 && c->steps > 0)
@@ -688,7 +701,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   if (s != LBM_OK) return s;
   const size_t fb = (size_t)c->sh.elems * elem_bytes(c->storage);
   const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
-  const size_t ub = sizeof(double) * 2 * MAX_BLOCKS;
+  const size_t ub = sizeof(long long) * 2 * MAX_BLOCKS;
   std::vector<unsigned char> payload(fb + sb + ub);
   CK(c, cudaMemcpy(payload.data(), c->fbuf(c->cur), fb, cudaMemcpyDeviceToHost));
   CK(c, cudaMemcpy(payload.data() + fb, c->stats(), sb, cudaMemcpyDeviceToHost));
@@ -696,7 +709,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "LBMB300\0", 8);
-  h.version = 2;
+  h.version = 3;
   h.storage = c->storage;
   h.nbins = c->nbins;
   h.grid = c->grid;
@@ -732,10 +745,10 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
   CkptHeader h;
   const size_t fb = (size_t)c->sh.elems * elem_bytes(c->storage);
   const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
-  const size_t ub = sizeof(double) * 2 * MAX_BLOCKS;
+  const size_t ub = sizeof(long long) * 2 * MAX_BLOCKS;
   std::vector<unsigned char> payload;
   bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, "LBMB300\0", 8) == 0 &&
-            h.version == 2 && h.storage == c->storage && h.nbins == c->nbins &&
+            h.version == 3 && h.storage == c->storage && h.nbins == c->nbins &&
             std::memcmp(&h.grid, &c->grid, sizeof(lbm_grid)) == 0 &&
             h.payload_bytes == fb + sb + ub && h.last_grid >= 0 && h.last_grid <= MAX_BLOCKS;
   if (ok) {
@@ -752,6 +765,7 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
   CK(c, cudaMemcpy(c->fbuf(0), payload.data(), fb, cudaMemcpyHostToDevice));
   CK(c, cudaMemcpy(c->stats(), payload.data() + fb, sb, cudaMemcpyHostToDevice));
   CK(c, cudaMemcpy(c->ub_part(), payload.data() + fb + sb, ub, cudaMemcpyHostToDevice));
+  CK(c, cudaMemset(c->state()->tile_ctr, 0, sizeof(DevState::tile_ctr)));  // fresh tile counters
   c->cur = 0;
   c->steps = h.steps;
   c->stats_samples = h.stats_samples;

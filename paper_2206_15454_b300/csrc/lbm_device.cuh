@@ -75,6 +75,7 @@ template <> struct Store<2> {
 struct DevState {
   unsigned int nan_flag;      // set when a cell produced a non-finite value
   unsigned int timeout_flag;  // set when a bounded device wait gave up
+  unsigned int tile_ctr[2];   // dynamic tile counters, one per step parity
 };
 
 constexpr int MAX_BLOCKS = 4096;  // per-block bulk-velocity partials per slot
@@ -112,7 +113,7 @@ struct StepParams {
   int ctrl;                 // bulk-velocity controller on
   int have_prev;            // a previous step measured U_b
   double g0x, gain, u_target, inv_cells;
-  double* ub_part;          // [2][MAX_BLOCKS] per-block sums of u_x, slot = step parity
+  long long* ub_part;       // [2][MAX_BLOCKS] per-block sums of u_x in 2^-32 fixed point, slot = step parity
   int slot_read, slot_write, nprev;  // nprev: blocks of the previous launch
   int canopy_x0, canopy_x1;
   const float* kdrag;       // ny values C_D a(y), or nullptr
@@ -123,6 +124,11 @@ struct StepParams {
   int nzg;
   long long ntiles;
   int nstage;               // tiles in flight per block
+  // work split of one domain: block b first walks the static run of tiles
+  // [b * static_tiles, (b + 1) * static_tiles), then takes tiles one by one
+  // from [gridDim.x * static_tiles, ntiles) through tile_ctr[ctr_slot]
+  int static_tiles;
+  int ctr_slot;
   // statistics
   double* stats;            // [9][nbins][ny] FP64 sums
   int nbins;
@@ -305,15 +311,17 @@ __device__ __forceinline__ float drag_factor(const StepParams& p, int x, int y) 
 }
 
 // Controller input: the bulk velocity of the previous step, summed by one
-// warp from that step's per-block partials in a fixed order (every block gets
-// the same value, and reruns are bitwise reproducible).  Call with a full warp.
+// warp from that step's per-block partials.  Every cell adds its u_x in
+// 2^-32 fixed point, so the integer sums are exact whichever block handled
+// which tile: every block gets the same value and reruns are bitwise
+// reproducible.  Call with a full warp.
 __device__ __forceinline__ double prev_bulk_velocity(const StepParams& p, int lane) {
-  const double* part = p.ub_part + (long long)p.slot_read * MAX_BLOCKS;
-  double s = 0.0;
+  const long long* part = p.ub_part + (long long)p.slot_read * MAX_BLOCKS;
+  long long s = 0;
   for (int k = lane; k < p.nprev; k += 32) s += part[k];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s * p.inv_cells;
+  return (double)s * (1.0 / 4294967296.0) * p.inv_cells;
 }
 
 __device__ __forceinline__ float controlled_gx(const StepParams& p, int lane) {
@@ -327,57 +335,53 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Plane statistics: reduce the per-thread sums (warp, then shared memory) and
-// add them to the FP64 accumulators of row y.  Called by every thread.
-__device__ __forceinline__ void flush_plane_stats(const StepParams& p, float* q, int& last_x,
-                                                  int y, float* s_stats, int lane, int tid,
-                                                  int nthreads) {
-  // warp-level reduction when the warp shares one x-bin, else per lane
+// Plane statistics of one warp: its lanes' sums for row y (taken from the
+// shared-memory slots `qs`, stride 256, and cleared) are added to the FP64
+// accumulators, one warp-reduced add per quantity when the lanes share an
+// x-bin, else one add per lane.  Called by every lane; no block barrier.
+__device__ __forceinline__ void flush_warp_stats(const StepParams& p, float* qs, int& last_x, int y,
+                                                 int lane) {
+  float q[9];
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    q[k] = qs[k * 256];
+    qs[k * 256] = 0.f;
+  }
   const int bin = last_x >= 0 ? (int)(((long long)last_x * p.nbins) / p.nx) : -1;
   const unsigned act = __ballot_sync(0xffffffffu, bin >= 0);
   if (act) {
     const int b0 = __shfl_sync(0xffffffffu, bin, __ffs(act) - 1);
-    const int key = bin >= 0 ? bin : b0;
-    const unsigned same = __match_any_sync(0xffffffffu, key);
-    if (same == 0xffffffffu) {
+    const long long m = (long long)p.nbins * p.ny;
+    double* acc = p.stats + (long long)y;
+    if (__all_sync(0xffffffffu, bin < 0 || bin == b0)) {
 #pragma unroll
-      for (int kk = 0; kk < 9; kk++) {
-        const float v = warp_sum(q[kk]);
-        if (lane == 0) atomicAdd(&s_stats[kk * p.nbins + key], v);
+      for (int k = 0; k < 9; k++) {
+        const float v = warp_sum(q[k]);
+        if (lane == 0) atomicAdd(acc + k * m + (long long)b0 * p.ny, (double)v);
       }
     } else if (bin >= 0) {
 #pragma unroll
-      for (int kk = 0; kk < 9; kk++) atomicAdd(&s_stats[kk * p.nbins + bin], q[kk]);
+      for (int k = 0; k < 9; k++) atomicAdd(acc + k * m + (long long)bin * p.ny, (double)q[k]);
     }
   }
-#pragma unroll
-  for (int kk = 0; kk < 9; kk++) q[kk] = 0.f;
   last_x = -1;
-  __syncthreads();
-  for (int kk = tid; kk < 9 * p.nbins; kk += nthreads) {
-    const float v = s_stats[kk];
-    if (v != 0.f) {
-      const int qk = kk / p.nbins, b = kk - qk * p.nbins;
-      atomicAdd(&p.stats[((long long)qk * p.nbins + b) * p.ny + y], (double)v);
-    }
-    s_stats[kk] = 0.f;
-  }
-  __syncthreads();
 }
 
-// Step epilogue: health flags and this block's share of the bulk velocity.
-__device__ __forceinline__ void finish_step(const StepParams& p, float ub_acc, bool bad, bool late,
-                                            float* s_ub, int lane, int warp, int tid,
-                                            int nthreads, int part) {
+// Step epilogue: health flags and this block's share of the bulk velocity
+// (exact integer sum of the fixed-point cell values).
+__device__ __forceinline__ void finish_step(const StepParams& p, long long ub_fix, bool bad,
+                                            bool late, long long* s_ub, int lane, int warp,
+                                            int tid, int nthreads, int part) {
   if (bad) atomicOr(&p.state->nan_flag, 1u);
   if (late) atomicOr(&p.state->timeout_flag, 1u);
-  const float w = warp_sum(ub_acc);
-  if (lane == 0) s_ub[warp] = w;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ub_fix += __shfl_xor_sync(0xffffffffu, ub_fix, o);
+  if (lane == 0) s_ub[warp] = ub_fix;
   __syncthreads();
   if (tid == 0 && part >= 0) {
-    double s = 0.0;
-    for (int kk = 0; kk < (nthreads + 31) / 32; kk++) s += (double)s_ub[kk];
-    p.ub_part[(long long)p.slot_write * MAX_BLOCKS + part] = s;
+    long long sum = 0;
+    for (int kk = 0; kk < (nthreads + 31) / 32; kk++) sum += s_ub[kk];
+    p.ub_part[(long long)p.slot_write * MAX_BLOCKS + part] = sum;
   }
 }
 
@@ -385,12 +389,14 @@ struct TileGeom {
   int xc, zg, y;
 };
 
+// tiles number fewer than cells (< 2^31): 32-bit arithmetic
 __device__ __forceinline__ TileGeom tile_geom(const StepParams& p, long long t) {
   TileGeom g;
-  g.xc = (int)(t % p.nxc);
-  const long long r = t / p.nxc;
-  g.zg = (int)(r % p.nzg);
-  g.y = (int)(r / p.nzg);
+  const unsigned tt = (unsigned)t, r = tt / (unsigned)p.nxc;
+  g.xc = (int)(tt - r * (unsigned)p.nxc);
+  const unsigned y = r / (unsigned)p.nzg;
+  g.zg = (int)(r - y * (unsigned)p.nzg);
+  g.y = (int)y;
   return g;
 }
 
@@ -404,6 +410,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // bulk copy global -> shared: 16-byte aligned addresses, size a multiple of 16
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -476,14 +485,13 @@ struct Stage {
 // stage: per tile row and direction, the chunk's cells of the source row plus
 // the ghost slot on the side its c_x streams from (16 bytes on that side).
 template <int XT, int S>
-__device__ __forceinline__ void issue_tile(const StepParams& p, long long t, unsigned char* stage,
-                                        uint64_t* bar, int lane) {
+__device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& g,
+                                           unsigned char* stage, uint64_t* bar, int lane) {
   using T = typename Store<S>::T;
   using Gm = Geo<XT, S>;
   using St = Stage<XT, S>;
   constexpr int H = St::H;
   constexpr uint64_t kCX = pack_comp(0), kCY = pack_comp(1), kCZ = pack_comp(2);
-  const TileGeom g = tile_geom(p, t);
   const int ry = blockDim.y;
   const int nrows = min(ry, p.nz - g.zg * ry);
   const int n = min(XT, p.nx - g.xc * XT);
@@ -527,20 +535,21 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, long long t, uns
 // data, so the copies are issued by a warp with time to spare and no
 // block-wide barrier sits in the loop.
 template <int XT, int S, bool STATS>
-__device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part) {
+__device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part,
+                                           bool dynamic) {
   using T = typename Store<S>::T;
   using Gm = Geo<XT, S>;
   using St = Stage<XT, S>;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ float s_stats[9 * MAX_XBINS];
   // per-thread statistics sums, kept in shared memory rather than registers
   // (the collision needs every register the three-blocks-per-SM budget allows)
   __shared__ float s_q[STATS ? 9 * 256 : 1];
-  __shared__ float s_ub[32];
+  __shared__ long long s_ub[8];
   __shared__ float s_gx;
   __shared__ __align__(8) uint64_t s_bar[8];
   __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
-  __shared__ int s_fill;              // next tile (block-local index) to copy in
+  __shared__ int s_fill;              // next fill (block-local sequence number) to issue
+  __shared__ int4 s_geo[8];           // (xc, zg, y, 1) of the tile each stage holds; y < 0: none
 
   const int tx = threadIdx.x;
   const int tid = threadIdx.y * XT + tx;
@@ -548,17 +557,20 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned int nwarps = (unsigned int)nthreads / 32;
   const int stage_bytes = (int)blockDim.y * NQ * St::SROW * (int)sizeof(T);
+  // s_fill: the next fill's sequence number; kBusy is or-ed in while a warp
+  // is choosing that fill's tile (one choice at a time, so dynamic tiles are
+  // taken in fill order); kNoMoreFills once a fill came back empty
+  constexpr int kBusy = 1 << 29, kNoMoreFills = 1 << 30;
 
   if (tid == 0) {
     for (int k = 0; k < p.nstage; k++) {
       mbar_init(&s_bar[k], 1);
       s_done[k] = 0;
     }
-    s_fill = min(p.nstage, ntile);
+    s_fill = p.nstage;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (STATS) {
-    for (int k = tid; k < 9 * p.nbins; k += nthreads) s_stats[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; k++) s_q[k * 256 + tid] = 0.f;
   }
@@ -568,10 +580,44 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   // are no-ops for an ordinary launch).
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  // Tile of the j-th fill (lane 0): the static run first, then (dynamic) one
+  // tile at a time from the step's counter; -1 once none is left.
+  auto tile_of_fill = [&](int j) -> long long {
+    if (j < ntile) return t0l + j;
+    if (!dynamic) return -1;
+    const long long t = (long long)gridDim.x * p.static_tiles +
+                        atomicAdd(&p.state->tile_ctr[p.ctr_slot], 1u);
+    return t < p.ntiles ? t : -1;
+  };
+  // Fill stage rs with the j-th tile (whole warp): lane 0 picks the tile,
+  // publishes its geometry (released by the mbarrier arrive) and, for a
+  // claimed fill, hands the next fill on; the lanes issue the copies.  With no
+  // tile left the stage completes empty and no further fill is claimed.
+  auto fill = [&](int j, int rs, bool claimed) {
+    TileGeom g{0, 0, -1};
+    if (lane == 0) {
+      const long long t = tile_of_fill(j);
+      if (t >= 0) {
+        g = tile_geom(p, t);
+        s_geo[rs] = make_int4(g.xc, g.zg, g.y, 1);
+        if (claimed) *reinterpret_cast<volatile int*>(&s_fill) = j + 1;
+      } else {
+        s_geo[rs] = make_int4(0, 0, -1, 0);
+        *reinterpret_cast<volatile int*>(&s_fill) = kNoMoreFills;
+        mbar_arrive(&s_bar[rs]);
+      }
+    }
+    g.xc = __shfl_sync(0xffffffffu, g.xc, 0);
+    g.zg = __shfl_sync(0xffffffffu, g.zg, 0);
+    g.y = __shfl_sync(0xffffffffu, g.y, 0);
+    if (g.y >= 0) issue_tile<XT, S>(p, g, smem + rs * stage_bytes, &s_bar[rs], lane);
+  };
+
+  if (tid == 0 && dynamic && blockIdx.x == 0) p.state->tile_ctr[1 - p.ctr_slot] = 0u;  // next step's
   __syncthreads();
   if (warp == 0) {
-    for (int k = 0; k < p.nstage && k < ntile; k++)
-      issue_tile<XT, S>(p, t0l + k, smem + k * stage_bytes, &s_bar[k], lane);
+    for (int k = 0; k < p.nstage; k++) fill(k, k, false);
     const float v = controlled_gx(p, lane);
     if (lane == 0) s_gx = v;
   }
@@ -586,37 +632,31 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
     int j = -1;
     if (lane == 0) {
       const int jn = *reinterpret_cast<volatile int*>(&s_fill);
-      if (jn < ntile) {
+      if (jn < kBusy) {
         const unsigned need = (unsigned)(jn / p.nstage) * nwarps;
         const unsigned done = *reinterpret_cast<volatile unsigned*>(&s_done[jn % p.nstage]);
-        if (done >= need && atomicCAS(&s_fill, jn, jn + 1) == jn) j = jn;
+        if (done >= need && atomicCAS(&s_fill, jn, jn | kBusy) == jn) j = jn;
       }
     }
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= 0) {
-      const int rs = j % p.nstage;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_tile<XT, S>(p, t0l + j, smem + rs * stage_bytes, &s_bar[rs], lane);
+      fill(j, j % p.nstage, true);
     }
   };
 
-  TileGeom g = tile_geom(p, t0l);
-  float ub_acc = 0.f;
+  long long ub_fix = 0;  // sum of u_x over this thread's cells, 2^-32 fixed point
   bool bad = false, late = false;
   float* const qs = s_q + tid;  // this thread's 9 sums, stride 256
   int last_x = -1;  // column of the last cell this thread accumulated (-1: none)
-  // with one x-chunk per row a thread keeps its column, so its x-bin is fixed
-  const bool flush_each_tile = p.nbins > 1 && p.nxc > 1;
+  int stat_y = -1;  // row the sums in qs belong to
+  int stat_xc = -1;
+  const bool flush_on_chunk = p.nbins > 1 && p.nxc > 1;
 
-  for (int t = 0; t < ntile; t++) {
+  for (int t = 0;; t++) {
     const int st = t % p.nstage;
     const uint32_t parity = (uint32_t)((t / p.nstage) & 1);
     const unsigned char* stage = smem + st * stage_bytes;
-    const int x0 = g.xc * XT;
-    const int x = x0 + tx;
-    const int z = g.zg * blockDim.y + threadIdx.y;
-    const int y = g.y;
-    const bool active = (x < p.nx) && (z < p.nz);
 
     try_refill();
     bool ready = false;
@@ -627,10 +667,25 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       }
       try_refill();
     }
-    if (!ready) late = true;
+    if (!ready) {
+      late = true;
+      break;
+    }
+    const int4 gq = s_geo[st];  // published by the fill (mbarrier release/acquire)
+    if (gq.z < 0) break;        // no tile left for this block
+    const int xc = gq.x, y = gq.z;
+    const int x = xc * XT + tx;
+    const int z = gq.y * blockDim.y + threadIdx.y;
+    const bool active = (x < p.nx) && (z < p.nz);
+    if (STATS && (y != stat_y || (flush_on_chunk && xc != stat_xc))) {
+      if (stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+      stat_y = y;
+      stat_xc = xc;
+    }
+
     float f[NQ];
     Macro m;
-    if (active && ready) {
+    if (active) {
       const T* sm = reinterpret_cast<const T*>(stage) + threadIdx.y * NQ * St::SROW + St::H + tx;
       // streaming from the staged rows; at a free-slip top the staged row is
       // already the mirrored one, so only bounce-back (own column) and the
@@ -660,9 +715,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
     // release the stage: the moments consumed every staged value of this warp
     __syncwarp();
     if (lane == 0) atomicAdd(&s_done[st], 1u);
-    if (active && ready) {
+    if (active) {
       const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
-      T* out = dst + (long long)(unsigned)(crow0 + g.xc) * Gm::ROW;
+      T* out = dst + (long long)(unsigned)(crow0 + xc) * Gm::ROW;
       // ghost slots this cell feeds (edge lanes only): its c_x = +1 values to
       // the left ghost of the chunk on its right, its c_x = -1 values to the
       // right ghost of the chunk on its left (periodic wrap), or beside itself
@@ -674,7 +729,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           if (!p.x_io) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
           else gl = out + 1;
         } else if (tx == XT - 1) {
-          gr = dst0 + (long long)(unsigned)(crow0 + g.xc + 1) * Gm::ROW - 1;
+          gr = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
         }
         if (x == 0) {
           if (!p.x_io) {
@@ -682,7 +737,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
             gl = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
           }
         } else if (tx == 0) {
-          gl = dst0 + (long long)(unsigned)(crow0 + g.xc - 1) * Gm::ROW + XT;
+          gl = dst0 + (long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT;
         }
       }
       collide(f, m, p.tau0, p.c18, [&](int i, float v) {
@@ -690,7 +745,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
         if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
       });
-      ub_acc += m.ux;
+      ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
       bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
       if (STATS) {
         qs[0 * 256] += m.ux; qs[1 * 256] += m.uy; qs[2 * 256] += m.uz;
@@ -699,31 +754,16 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         last_x = x;
       }
     }
-    // advance to the next tile; flush the plane statistics when y changes
-    const int y_now = g.y;
-    if (++g.xc == p.nxc) {
-      g.xc = 0;
-      if (++g.zg == p.nzg) { g.zg = 0; ++g.y; }
-    }
-    if (STATS && (g.y != y_now || t + 1 == ntile || flush_each_tile)) {
-      float q[9];
-#pragma unroll
-      for (int k = 0; k < 9; k++) {
-        q[k] = qs[k * 256];
-        qs[k * 256] = 0.f;
-      }
-      flush_plane_stats(p, q, last_x, y_now, s_stats, lane, tid, nthreads);
-    }
   }
-  finish_step(p, ub_acc, bad, late, s_ub, lane, warp, tid, nthreads, part);
+  if (STATS && stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+  finish_step(p, ub_fix, bad, late, s_ub, lane, warp, tid, nthreads, part);
 }
 
-// One domain: block b takes the b-th of gridDim.x equal runs of its tiles.
+// One domain: block b walks its static run of tiles, then shares the rest.
 template <int XT, int S, bool STATS>
 __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
-  const long long t0l = (long long)blockIdx.x * p.ntiles / gridDim.x;
-  const int ntile = (int)((long long)(blockIdx.x + 1) * p.ntiles / gridDim.x - t0l);
-  step_tiles<XT, S, STATS>(p, t0l, ntile, blockIdx.x);
+  step_tiles<XT, S, STATS>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles, blockIdx.x,
+                           true);
 }
 
 // Many independent domains (an ensemble of boxes) in one launch: work item
@@ -748,7 +788,7 @@ __global__ void __launch_bounds__(256, 3) batch_step_kernel(const StepParams* __
       dst[k] = src[k];
   }
   __syncthreads();
-  step_tiles<XT, S, STATS>(s_p, w.t0, w.ntile, -1);
+  step_tiles<XT, S, STATS>(s_p, w.t0, w.ntile, -1, false);
 }
 
 // ---- ghost slots from the cells (after init, set_f) ----------------------------------
