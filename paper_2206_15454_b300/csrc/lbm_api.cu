@@ -345,17 +345,35 @@ void launch_macro(const lbm_ctx* c, const StepParams& p, float* out) {
   macro_kernel<XT, S><<<c->sm_count * 8, 256, 0, c->stream>>>(p, out);
 }
 
-// The learned correction over all first-cell columns: with th, the layer-0
-// acceleration for the next step; with th == nullptr, the raw features into X.
+// The correction's inputs over all first-cell columns into X, and with th
+// the network's layer-0 acceleration for the next step from them.
 void launch_correction(const lbm_ctx* c, const float* th, float* X) {
   const StepParams p = make_params(c);
   const long long cols = (long long)c->grid.nx * c->grid.nz;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((cols + 127) / 128,
-                                                                     (long long)c->sm_count * 8));
+  const int fblocks = (int)std::max<long long>(1, std::min<long long>((cols + 255) / 256,
+                                                                      (long long)c->sm_count * 16));
   dispatch(c, [&](auto xt, auto s) {
-    correction_kernel<decltype(xt)::value, decltype(s)::value>
-        <<<blocks, 128, 0, c->stream>>>(p, th, c->lam, c->accel(), X);
+    features_kernel<decltype(xt)::value, decltype(s)::value><<<fblocks, 256, 0, c->stream>>>(p, X);
   });
+  if (th) {
+    const long long tiles = (cols + 15) / 16;
+    // few blocks, many rows each: every block stages the weights once
+    const int mblocks = (int)std::max<long long>(1, std::min<long long>((tiles + 3) / 4,
+                                                                        (long long)c->sm_count * 2));
+    mlp_accel_kernel<<<mblocks, 128, 0, c->stream>>>(th, X, cols, c->lam, c->accel());
+  }
+}
+
+// The feature staging buffer (nx*nz rows of 9 floats), allocated on first use.
+lbm_status ensure_feat_buf(lbm_ctx* c) {
+  if (c->feat_buf) return LBM_OK;
+  const size_t cols = (size_t)c->grid.nx * c->grid.nz;
+  if (cudaMalloc(&c->feat_buf, sizeof(float) * cols * MLP_IN) != cudaSuccess) {
+    cudaGetLastError();
+    c->feat_buf = nullptr;
+    return fail(c, LBM_ERR_OOM, "cudaMalloc of the correction's feature buffer failed");
+  }
+  return LBM_OK;
 }
 
 lbm_status check_device(lbm_ctx* c) {
@@ -526,7 +544,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     if (c->stats_on) c->stats_samples++;
     if (c->mlp) {
       // the next step's layer-0 acceleration from the new state
-      launch_correction(c, c->mlp->theta, nullptr);
+      launch_correction(c, c->mlp->theta, c->feat_buf);
       CK(c, cudaGetLastError());
     }
   }
@@ -1502,11 +1520,15 @@ lbm_status lbm_set_correction(lbm_ctx* c, const lbm_mlp* m, double lam) {
   if (c->batch) return arg_error(c, "lbm_set_correction: not available for ensemble boxes");
   if (m && c->grid.ny < 3) return arg_error(c, "lbm_set_correction: needs ny >= 3");
   if (!std::isfinite(lam)) return arg_error(c, "lbm_set_correction: lam not finite");
+  if (m) {
+    lbm_status s = ensure_feat_buf(c);
+    if (s != LBM_OK) return s;
+  }
   c->mlp = m;
   c->lam = (float)lam;
   if (m) {
     CK(c, cudaStreamSynchronize(m->stream));  // the network's parameters are ready
-    launch_correction(c, m->theta, nullptr);
+    launch_correction(c, m->theta, c->feat_buf);
     CK(c, cudaGetLastError());
   }
   return LBM_OK;
@@ -1517,13 +1539,8 @@ lbm_status lbm_features(lbm_ctx* c, float* X, size_t n) {
   const size_t cols = (size_t)c->grid.nx * c->grid.nz;
   if (!X || n != cols * MLP_IN) return arg_error(c, "lbm_features: wrong size");
   if (c->grid.ny < 3) return arg_error(c, "lbm_features: needs ny >= 3");
-  if (!c->feat_buf) {
-    if (cudaMalloc(&c->feat_buf, sizeof(float) * cols * MLP_IN) != cudaSuccess) {
-      cudaGetLastError();
-      c->feat_buf = nullptr;
-      return fail(c, LBM_ERR_OOM, "lbm_features: cudaMalloc of the feature buffer failed");
-    }
-  }
+  lbm_status s0 = ensure_feat_buf(c);
+  if (s0 != LBM_OK) return s0;
   launch_correction(c, nullptr, c->feat_buf);
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);

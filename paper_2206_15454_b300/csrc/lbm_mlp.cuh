@@ -224,51 +224,49 @@ __device__ __forceinline__ void column_features(const StepParams& p, float gx, i
   }
 }
 
-// Per column of the domain: features -> network -> layer-0 acceleration for
-// the next step (or, with X_out, the raw features themselves).
+// Column features of the whole first layer: X[c][9] for c = z * nx + x.
 template <int XT, int S>
-__global__ void __launch_bounds__(128) correction_kernel(StepParams p, const float* __restrict__ th,
-                                                         float lam, float2* __restrict__ accel,
-                                                         float* __restrict__ X_out) {
+__global__ void __launch_bounds__(256) features_kernel(StepParams p, float* __restrict__ X) {
+  const float gx = controlled_gx(p, threadIdx.x & 31);  // blockDim.x is a multiple of 32
+  const long long ncol = (long long)p.nx * p.nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncol;
+       c += (long long)gridDim.x * blockDim.x) {
+    float feat[MLP_IN];
+    column_features<XT, S>(p, gx, (int)(c % p.nx), (int)(c / p.nx), feat);
+#pragma unroll
+    for (int k = 0; k < MLP_IN; k++) X[c * MLP_IN + k] = feat[k];
+  }
+}
+
+// The network on feature rows X[n][9] (tensor cores), written as the layer-0
+// acceleration a = (lam du_x - dtau_x, lam du_z - dtau_z) of each row.
+__global__ void __launch_bounds__(128) mlp_accel_kernel(const float* __restrict__ th,
+                                                        const float* __restrict__ X, long long n,
+                                                        float lam, float2* __restrict__ accel) {
   __shared__ MlpSmem s;
-  __shared__ __align__(16) __nv_bfloat16 xin[4][2][16 * 16];
-  if (th != nullptr) mlp_stage(s, th);
+  __shared__ __align__(16) __nv_bfloat16 xin[4][16 * 16];
+  mlp_stage(s, th);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float gx = controlled_gx(p, lane);
-  const long long ncol = (long long)p.nx * p.nz;
-  const long long tiles = (ncol + 31) / 32;  // 32 columns per warp iteration
+  const long long tiles = (n + 15) / 16;
   for (long long tile = (long long)blockIdx.x * 4 + warp; tile < tiles; tile += (long long)gridDim.x * 4) {
-    const long long c = tile * 32 + lane;  // column index z * nx + x
-    float feat[MLP_IN];
-    if (c < ncol) {
-      column_features<XT, S>(p, gx, (int)(c % p.nx), (int)(c / p.nx), feat);
-    } else {
-#pragma unroll
-      for (int k = 0; k < MLP_IN; k++) feat[k] = 0.f;
-    }
-    if (X_out != nullptr) {
-      if (c < ncol)
-#pragma unroll
-        for (int k = 0; k < MLP_IN; k++) X_out[c * MLP_IN + k] = feat[k];
-      continue;
-    }
     __syncwarp();
-    __nv_bfloat16* mine = xin[warp][lane >> 4] + (lane & 15) * 16;
+    if (lane < 16) {
+      const long long r = tile * 16 + lane;
 #pragma unroll
-    for (int k = 0; k < 16; k++)
-      mine[k] = __float2bfloat16_rn(k < MLP_IN ? (feat[k] - s.xm[k]) * s.xinv[k] : 0.f);
-    __syncwarp();
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      float o[4], r0[4], r1[4];
-      mlp_rows16(s, xin[warp][h], lane, o);
-      mlp_gather_outputs(s, o, lane, r0, r1);
-      if ((lane & 3) == 0) {
-        const long long ca = tile * 32 + h * 16 + (lane >> 2), cb = ca + 8;
-        if (ca < ncol) accel[ca] = make_float2(lam * r0[0] - r0[2], lam * r0[1] - r0[3]);
-        if (cb < ncol) accel[cb] = make_float2(lam * r1[0] - r1[2], lam * r1[1] - r1[3]);
+      for (int k = 0; k < 16; k++) {
+        const float v = (r < n && k < MLP_IN) ? (X[r * MLP_IN + k] - s.xm[k]) * s.xinv[k] : 0.f;
+        xin[warp][lane * 16 + k] = __float2bfloat16_rn(v);
       }
+    }
+    __syncwarp();
+    float o[4], r0[4], r1[4];
+    mlp_rows16(s, xin[warp], lane, o);
+    mlp_gather_outputs(s, o, lane, r0, r1);
+    if ((lane & 3) == 0) {
+      const long long ra = tile * 16 + (lane >> 2), rb = ra + 8;
+      if (ra < n) accel[ra] = make_float2(lam * r0[0] - r0[2], lam * r0[1] - r0[3]);
+      if (rb < n) accel[rb] = make_float2(lam * r1[0] - r1[2], lam * r1[1] - r1[3]);
     }
   }
 }
