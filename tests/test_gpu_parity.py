@@ -251,3 +251,35 @@ def test_turbulent_statistics_within_2_percent(name, case):
           + " ".join(f"{k}={v:.2e}" for k, v in err.items()))
     for k, v in err.items():
         assert v < 0.02, (k, v)
+
+
+@pytest.mark.parametrize("forest", [1, 2, 3])
+def test_paper_abl_forest_cases_match_oracle(forest):
+    """The paper's ABL set-up (periodic x/z, forced-equilibrium top, body force)
+    with the three forest cases of Table tab:forest_cases, 100 steps."""
+    case = W.abl_forest(forest, nx=40, ny=16, nz=12)
+    d, o = pair(case)
+    d.step(100)
+    o.step(100)
+    err = rel_l2(d.get_f(), o.get_f())
+    assert err <= F32_TOL, (forest, err)
+
+
+def test_paper_abl_forest_profiles_are_ordered():
+    """Profile comparison of the three forest cases (same seed and driving):
+    inside the forest the modelled drag slows the flow, so after the same time
+    the no-forest case is fastest there, and the two forest cases (equal total
+    obstruction by design, close as implemented) stay close to each other."""
+    means = {}
+    for forest in (1, 2, 3):
+        case = W.abl_forest(forest, nx=80, ny=32, nz=64)
+        d = P.Domain(case)
+        d.step(1500)
+        d.stats_reset(True)
+        d.step(500)
+        s, _ = d.stats()
+        h = int(round(20.0 / (400.0 / case.ny)))
+        means[forest] = (s[0, 0, :h].mean(), s[0, 0, 2 * h:4 * h].mean())
+    print({k: tuple(round(float(x), 5) for x in v) for k, v in means.items()})
+    assert means[3][0] > 1.2 * max(means[1][0], means[2][0])
+    assert abs(means[1][0] - means[2][0]) < 0.5 * means[3][0]

@@ -144,6 +144,37 @@ def canopy_abl(nx=512, ny=128, nz=256, h=10.0, a=0.2, cd=0.15, canopy_x0=128,
                 u_profile=log_law_inflow(ny, u_inf))
 
 
+def abl_forest(case: int = 1, nx: int = 160, ny: int = 64, nz: int = 128,
+               u_top: float = 0.05, tau0: float = 0.501, xbin: int = 1) -> Case:
+    """The paper's atmospheric boundary layer over a forest (Sec. 5): a
+    1000 x 400 x 800 m domain (nx, ny, nz cells, dx = 400 m / ny), periodic in x
+    and z, no-slip (bounce-back) ground, forced-equilibrium top moving with the
+    free stream u_top, a forest of height 20 m over the whole ground, driven by a
+    uniform body force.  Forest cases of Table tab:forest_cases: 1 = constant
+    LAD 0.215 per m, 2 = Eq. af_theory with a_m = 0.38 per m at y_m = 0.7 h,
+    3 = no forest.  LAD per lattice length = LAD per m * dx.  The body force
+    balances a friction velocity u_* = 0.1 u_top over the domain height
+    (g = u_*^2 / ny): the paper's non-dimensional force value is not used
+    (its normalisation is ambiguous as printed)."""
+    dx = 400.0 / ny
+    h = 20.0 / dx
+    if case == 1:
+        lad = lad_constant(ny, 0.215 * dx, h)
+    elif case == 2:
+        lad = lad_lalic_cells(ny, 0.38 * dx, 0.7 * h, h)
+    elif case == 3:
+        lad = None
+    else:
+        raise ValueError("forest case is 1, 2 or 3")
+    u_star = 0.1 * u_top
+    return Case(f"abl_forest{case}", nx, ny, nz, bc_y=(BOUNCEBACK, EQUILIBRIUM), tau0=tau0,
+                cs=0.1, g=(u_star ** 2 / ny, 0.0, 0.0), cd=0.15 if lad is not None else 0.0,
+                canopy_x=(0, nx) if lad is not None else (0, 0), u_top=(u_top, 0.0, 0.0),
+                stats_xbins=max(1, nx // max(1, xbin)) if xbin > 1 else 1,
+                seed=SEED_BASE + 10 + case, init_perturb=0.05 * u_top,
+                lad=lad, u_profile=log_law_inflow(ny, u_top))
+
+
 def ensemble_boxes(n_boxes=64, ny=64, nz=64, nx_range=(96, 160), seed=SEED_BASE + 4,
                    u_tau=0.003, tau0=0.501) -> Sequence[Case]:
     """Independent canopy boxes of uneven x-length with seeded Gaussian LAD."""
