@@ -126,6 +126,7 @@ struct lbm_ctx {
   const lbm_mlp* mlp = nullptr;  // learned first-layer correction in use, if any
   float lam = 0.f;               // its velocity relaxation rate
   float* feat_buf = nullptr;     // staging buffer of lbm_features
+  unsigned char* readout = nullptr;  // pinned host copy of the statistics and health flags
 
   void* fbuf(int k) const { return ws + (size_t)k * L.f_bytes; }
   double* stats() const { return reinterpret_cast<double*>(ws + L.stats_off); }
@@ -569,10 +570,25 @@ lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
   const int ny = c->grid.ny, nb = c->nbins, nx = c->grid.nx;
   const size_t m = (size_t)nb * ny;
   if (!out || n < 9 * m) return arg_error(c, "lbm_stats: output too small");
-  lbm_status s = check_device(c);
-  if (s != LBM_OK) return s;
-  std::vector<double> acc(9 * m);
-  CK(c, cudaMemcpy(acc.data(), c->stats(), sizeof(double) * acc.size(), cudaMemcpyDeviceToHost));
+  // one asynchronous copy of the statistics and the health flags (adjacent in
+  // the workspace) into pinned memory, then one wait on the context's stream
+  const size_t bytes = c->L.state_off + sizeof(DevState) - c->L.stats_off;
+  if (!c->readout) {
+    if (cudaMallocHost(&c->readout, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->readout = nullptr;
+      return fail(c, LBM_ERR_OOM, "lbm_stats: cudaMallocHost of the readout buffer failed");
+    }
+  }
+  CK(c, cudaMemcpyAsync(c->readout, c->ws + c->L.stats_off, bytes, cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaGetLastError());
+  const DevState* st = reinterpret_cast<const DevState*>(c->readout + (c->L.state_off - c->L.stats_off));
+  if (st->timeout_flag)
+    return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
+  if (st->nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density or velocity");
+  const double* acc = reinterpret_cast<const double*>(c->readout);
   std::vector<long long> width(nb, 0);
   for (int x = 0; x < nx; x++) width[(long long)x * nb / nx]++;
   for (int b = 0; b < nb; b++)
@@ -842,6 +858,7 @@ void lbm_destroy(lbm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->macro_buf) cudaFree(c->macro_buf);
   if (c->feat_buf) cudaFree(c->feat_buf);
+  if (c->readout) cudaFreeHost(c->readout);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   delete c;
 }

@@ -283,3 +283,17 @@ def test_paper_abl_forest_profiles_are_ordered():
     print({k: tuple(round(float(x), 5) for x in v) for k, v in means.items()})
     assert means[3][0] > 1.2 * max(means[1][0], means[2][0])
     assert abs(means[1][0] - means[2][0]) < 0.5 * means[3][0]
+
+
+def test_full_size_canopy_step_matches_oracle():
+    """The 512 x 128 x 256 forest-canopy boundary layer (inflow/outflow, 16.8 M
+    cells) in the benchmark's launch shape: two full steps against the oracle,
+    every population compared."""
+    case = W.canopy_abl()
+    d, o = pair(case)
+    d.step(2)
+    o.step(2)
+    fo = o.get_f()
+    o.close()
+    err = rel_l2(d.get_f(), fo)
+    assert err < F32_TOL, err
