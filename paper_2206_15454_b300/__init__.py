@@ -59,7 +59,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise LbmError(LBM_ERR_CUDA, f"CUDA library missing: {LIB_PATH} (run build())")
+            raise LbmError(LBM_ERR_CUDA, f"CUDA library missing: {LIB_PATH} (build it with python -m paper_2206_15454_b300.build)")
         L = C.CDLL(LIB_PATH)
         vp, st = C.c_void_p, C.c_int32
         L.lbm_workspace_bytes.restype = C.c_size_t
@@ -608,8 +608,3 @@ class Batch:
             self.close()
         except Exception:
             pass
-
-
-def build(force=False):
-    from . import build as _b
-    return _b.build(force=force)
