@@ -732,10 +732,11 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       // at an outflow (zero gradient)
       T* gr = nullptr;
       T* gl = nullptr;
+      T* go = nullptr;  // outflow: the last cell's own slot G + n (zero gradient)
       if (tx == 0 || tx == XT - 1 || x == p.nx - 1) {
         if (x == p.nx - 1) {
           if (!p.x_io) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
-          else gl = out + 1;
+          else go = out + 1;
         } else if (tx == XT - 1) {
           gr = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
         }
@@ -752,6 +753,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         Store<S>::st(out + i * Gm::XTP, v);
         if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
         if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
+        if (cx(i) == -1 && go) Store<S>::st(go + i * Gm::XTP, v);
       });
       ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
       bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
@@ -773,6 +775,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   step_tiles<XT, S, STATS>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles, blockIdx.x,
                            true);
 }
+
 
 // Many independent domains (an ensemble of boxes) in one launch: work item
 // w = (box, first tile, tiles) per block; the block runs the same tile loop

@@ -34,6 +34,9 @@ CASES = W.small_cases() + [
            init_perturb=0.01, seed=11),
     W.poiseuille(1, 32, 1).replace(name="column"),
     W.channel_les(300, 9, 5).replace(name="two_x_chunks"),  # nx > 256: two tiles per row
+    # inflow/outflow with a one-cell last chunk: that cell feeds both the
+    # previous chunk's ghost and its own outflow ghost
+    W.canopy_abl(257, 9, 5, h=3.0, canopy_x0=60, xbin=64).replace(name="outflow_one_cell_chunk"),
 ]
 
 
