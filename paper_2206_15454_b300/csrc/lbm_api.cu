@@ -243,6 +243,8 @@ StepParams make_params(const lbm_ctx* c) {
   p.ctr_slot = (int)(c->steps & 1);
   p.stats = c->stats();
   p.nbins = c->nbins;
+  p.xc_outer = c->nbins > 1 && c->sh.nxc > 1;
+  p.io_one = p.x_io && g.nx - (c->sh.nxc - 1) * c->sh.xt == 1;
   p.state = c->state();
   p.src = c->fbuf(c->cur);
   p.dst = c->fbuf(1 - c->cur);

@@ -106,6 +106,7 @@ struct StepParams {
   void* dst;
   int nx, ny, nz, nxc;      // nxc chunks of XT cells per row
   int x_io;                 // 1: inflow at x = 0, outflow at x = nx-1; 0: periodic
+  int io_one;               // x_io with a last chunk of one cell
   int y_walls;              // 1: bounce-back bottom + `top` kind; 0: periodic
   int top;                  // 1 bounce-back, 2 free-slip, 3 equilibrium
   float tau0, c18;          // c18 = 18 sqrt(2) C_s^2
@@ -120,8 +121,13 @@ struct StepParams {
   const float* lad;         // ny values a(y), or nullptr (inputs of the learned correction)
   const float* feq_in;      // [ny][19] shifted f_eq(1, u_in(y)) for the inflow column
   float feq_top[NQ];        // shifted f_eq(1, u_top) (equilibrium top)
-  // tiling: tile = (y, z-group, x-chunk), block = (XT, ry) threads
+  // tiling: tile = (y, z-group, x-chunk), block = (XT, ry) threads; tiles
+  // are numbered y-major, then z-group, then chunk, or with x-binned
+  // statistics over several chunks then chunk, then z-group (consecutive
+  // tiles of a block then share their x-bins, so its statistics sums are
+  // flushed when the chunk changes, not at every tile)
   int nzg;
+  int xc_outer;
   long long ntiles;
   int nstage;               // tiles in flight per block
   // work split of one domain: block b first walks the static run of tiles
@@ -392,10 +398,13 @@ struct TileGeom {
 // tiles number fewer than cells (< 2^31): 32-bit arithmetic
 __device__ __forceinline__ TileGeom tile_geom(const StepParams& p, long long t) {
   TileGeom g;
-  const unsigned tt = (unsigned)t, r = tt / (unsigned)p.nxc;
-  g.xc = (int)(tt - r * (unsigned)p.nxc);
-  const unsigned y = r / (unsigned)p.nzg;
-  g.zg = (int)(r - y * (unsigned)p.nzg);
+  // t = (y * n_mid + mid) * n_in + in, (in, mid) = (chunk, z-group) or swapped
+  const unsigned tt = (unsigned)t, n_in = p.xc_outer ? p.nzg : p.nxc,
+                 n_mid = p.xc_outer ? p.nxc : p.nzg;
+  const unsigned r = tt / n_in, y = r / n_mid;
+  const int in = (int)(tt - r * n_in), mid = (int)(r - y * n_mid);
+  g.xc = p.xc_outer ? mid : in;
+  g.zg = p.xc_outer ? in : mid;
   g.y = (int)y;
   return g;
 }
@@ -732,11 +741,10 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       // at an outflow (zero gradient)
       T* gr = nullptr;
       T* gl = nullptr;
-      T* go = nullptr;  // outflow: the last cell's own slot G + n (zero gradient)
       if (tx == 0 || tx == XT - 1 || x == p.nx - 1) {
         if (x == p.nx - 1) {
           if (!p.x_io) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
-          else go = out + 1;
+          else gl = out + 1;  // outflow: its own slot G + n (a one-cell last chunk: below)
         } else if (tx == XT - 1) {
           gr = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
         }
@@ -753,8 +761,15 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         Store<S>::st(out + i * Gm::XTP, v);
         if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
         if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
-        if (cx(i) == -1 && go) Store<S>::st(go + i * Gm::XTP, v);
       });
+      if (p.io_one && x == p.nx - 1) {
+        // a one-cell last chunk at an outflow: gl went to the previous
+        // chunk's right ghost, so the zero-gradient copy beside the cell is
+        // taken from the line it just stored
+#pragma unroll
+        for (int i = 0; i < NQ; i++)
+          if (cx(i) == -1) out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
+      }
       ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
       bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
       if (STATS) {
@@ -775,7 +790,6 @@ __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   step_tiles<XT, S, STATS>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles, blockIdx.x,
                            true);
 }
-
 
 // Many independent domains (an ensemble of boxes) in one launch: work item
 // w = (box, first tile, tiles) per block; the block runs the same tile loop
