@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-box ensemble leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction leg")
+    ap.add_argument("--no-canopy", action="store_true",
+                    help="skip the 512x128x256 canopy leg (x-binned statistics)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile", metavar="NXxNYxNZ|ensemble|learned", default=None,
                     help="run a few steps of the channel workload at this size (or of the "
@@ -239,10 +241,39 @@ def time_ensemble(P, W, steps, warmup, hbm):
            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                         "frac": round(ach / hbm, 4), "traffic": None},
            "tuning": {"chunk_width": xt, "blocks_per_launch": blocks,
-                      "padded_cells_fraction": round(cells / padded, 4),
+                      "fluid_fraction_of_tile_cells": round(cells / padded, 4),
                       "candidates": [{"chunk_width": c[0], "blocks": c[1], "ms_per_step": c[2]}
                                      for c in b.candidates()]}}
     b.close()
+    return out
+
+
+def time_canopy(P, W, steps, warmup, hbm):
+    """The forest-canopy boundary layer on 512x128x256 cells (inflow/outflow,
+    canopy over x in [128, 512), statistics per x-bin of 64 cells), FP32 and
+    FP16-shifted storage."""
+    import torch
+
+    case = W.canopy_abl()
+    out = {"workload": "canopy ABL 512x128x256 (h=10, a=0.2, C_D=0.15, inflow/outflow, "
+                       "statistics per x-bin of 64)", "cells": case.cells, "steps": steps}
+    for name, st in (("f32", P.LBM_F32), ("f16s", P.LBM_F16_SHIFTED)):
+        d = P.Domain(case, st)
+        d.stats_reset(True)
+        d.step(warmup)
+        d.sync()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(d.stream)
+        d.step(steps)
+        t1.record(d.stream)
+        torch.cuda.synchronize()
+        d.sync()
+        d.close()
+        ms = t0.elapsed_time(t1) / steps
+        ach = P.BYTES_PER_LUP[st] * case.cells / (ms * 1e-3) / 1e9
+        out[name] = {"value": round(case.cells / ms / 1e3, 1), "unit": "MLUPS", "ms_per_step": ms,
+                     "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                                  "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None}}
     return out
 
 
@@ -406,6 +437,8 @@ def run_ours(args):
                                       "unit": "GB/s", "frac": round(ach / hbm, 4),
                                       "traffic": measured_traffic(name, cells)},
                          "rel_l2_f_vs_f32_after_100_steps": err}
+    if not args.no_canopy:
+        res["canopy"] = time_canopy(P, W, min(args.steps, 500), max(args.warmup, 3), hbm)
     if not args.no_ensemble:
         res["ensemble"] = time_ensemble(P, W, min(args.steps, 1000), max(args.warmup, 3), hbm)
     if not args.no_learned:

@@ -63,7 +63,8 @@ typedef enum lbm_status {
     LBM_ERR_ARG = 1,      /* invalid argument; the context (if any) is unchanged */
     LBM_ERR_OOM = 2,      /* device or host allocation failed / workspace too small */
     LBM_ERR_CUDA = 3,     /* a CUDA runtime call failed */
-    LBM_ERR_NAN = 4,      /* a cell produced a non-finite density or velocity */
+    LBM_ERR_NAN = 4,      /* a cell produced a non-finite density (a non-finite velocity
+                             or population shows as one within a step) */
     LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
     LBM_ERR_STATE = 6,    /* the context holds an earlier sticky error */
     LBM_ERR_IO = 7        /* checkpoint file could not be written/read/verified */

@@ -243,7 +243,7 @@ StepParams make_params(const lbm_ctx* c) {
   p.ctr_slot = (int)(c->steps & 1);
   p.stats = c->stats();
   p.nbins = c->nbins;
-  p.xc_outer = c->nbins > 1 && c->sh.nxc > 1;
+  p.xc_outer = c->stats_on && c->nbins > 1 && c->sh.nxc > 1;
   p.io_one = p.x_io && g.nx - (c->sh.nxc - 1) * c->sh.xt == 1;
   p.state = c->state();
   p.src = c->fbuf(c->cur);
@@ -386,7 +386,7 @@ lbm_status check_device(lbm_ctx* c) {
   CK(c, cudaMemcpy(&st, c->state(), sizeof(st), cudaMemcpyDeviceToHost));
   if (st.timeout_flag)
     return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
-  if (st.nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density or velocity");
+  if (st.nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density");
   return LBM_OK;
 }
 
@@ -589,7 +589,7 @@ lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
   const DevState* st = reinterpret_cast<const DevState*>(c->readout + (c->L.state_off - c->L.stats_off));
   if (st->timeout_flag)
     return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
-  if (st->nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density or velocity");
+  if (st->nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density");
   const double* acc = reinterpret_cast<const double*>(c->readout);
   std::vector<long long> width(nb, 0);
   for (int x = 0; x < nx; x++) width[(long long)x * nb / nx]++;

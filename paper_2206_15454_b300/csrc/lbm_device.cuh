@@ -771,7 +771,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           if (cx(i) == -1) out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
       }
       ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
-      bad |= !(fabsf(m.drho) < 1e30f && fabsf(m.ux) + fabsf(m.uy) + fabsf(m.uz) < 1e30f);
+      // health: a non-finite density (a non-finite velocity or population
+      // makes the density non-finite by the next step at the latest)
+      bad |= !(fabsf(m.drho) < 1e30f);
       if (STATS) {
         qs[0 * 256] += m.ux; qs[1 * 256] += m.uy; qs[2 * 256] += m.uz;
         qs[3 * 256] += m.ux * m.ux; qs[4 * 256] += m.uy * m.uy; qs[5 * 256] += m.uz * m.uz;
