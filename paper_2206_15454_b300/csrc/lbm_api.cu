@@ -244,6 +244,11 @@ StepParams make_params(const lbm_ctx* c) {
   p.stats = c->stats();
   p.nbins = c->nbins;
   p.xc_outer = c->stats_on && c->nbins > 1 && c->sh.nxc > 1;
+  p.t_in = p.xc_outer ? p.nzg : p.nxc;
+  p.t_mid = p.xc_outer ? p.nxc : p.nzg;
+  p.t_in_inv = 1.0f / (float)p.t_in;
+  p.t_mid_inv = 1.0f / (float)p.t_mid;
+  p.t_fast = p.ntiles < (1ll << 23);
   p.io_one = p.x_io && g.nx - (c->sh.nxc - 1) * c->sh.xt == 1;
   p.state = c->state();
   p.src = c->fbuf(c->cur);

@@ -128,6 +128,8 @@ struct StepParams {
   // flushed when the chunk changes, not at every tile)
   int nzg;
   int xc_outer;
+  int t_in, t_mid, t_fast;  // tile-number radices (chunks / z-groups); t_fast: ntiles < 2^23
+  float t_in_inv, t_mid_inv;
   long long ntiles;
   int nstage;               // tiles in flight per block
   // work split of one domain: block b first walks the static run of tiles
@@ -396,12 +398,26 @@ struct TileGeom {
 };
 
 // tiles number fewer than cells (< 2^31): 32-bit arithmetic
+// t / n for t < 2^23 from a float reciprocal: the rounded quotient is off by
+// at most one, which the remainder corrects.
+__device__ __forceinline__ unsigned div_small(unsigned t, unsigned n, float inv) {
+  unsigned q = __float2uint_rz(__uint2float_rn(t) * inv);
+  const int r = (int)(t - q * n);
+  return r < 0 ? q - 1 : (r >= (int)n ? q + 1 : q);
+}
+
 __device__ __forceinline__ TileGeom tile_geom(const StepParams& p, long long t) {
   TileGeom g;
   // t = (y * n_mid + mid) * n_in + in, (in, mid) = (chunk, z-group) or swapped
-  const unsigned tt = (unsigned)t, n_in = p.xc_outer ? p.nzg : p.nxc,
-                 n_mid = p.xc_outer ? p.nxc : p.nzg;
-  const unsigned r = tt / n_in, y = r / n_mid;
+  const unsigned tt = (unsigned)t, n_in = p.t_in, n_mid = p.t_mid;
+  unsigned r, y;
+  if (p.t_fast) {
+    r = div_small(tt, n_in, p.t_in_inv);
+    y = div_small(r, n_mid, p.t_mid_inv);
+  } else {
+    r = tt / n_in;
+    y = r / n_mid;
+  }
   const int in = (int)(tt - r * n_in), mid = (int)(r - y * n_mid);
   g.xc = p.xc_outer ? mid : in;
   g.zg = p.xc_outer ? in : mid;
@@ -557,7 +573,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   __shared__ float s_gx;
   __shared__ __align__(8) uint64_t s_bar[8];
   __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
-  __shared__ int s_fill;              // next fill (block-local sequence number) to issue
+  __shared__ int s_fill;              // next fill to issue: 8 * round + stage
   __shared__ int4 s_geo[8];           // (xc, zg, y, 1) of the tile each stage holds; y < 0: none
 
   const int tx = threadIdx.x;
@@ -566,8 +582,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned int nwarps = (unsigned int)nthreads / 32;
   const int stage_bytes = (int)blockDim.y * NQ * St::SROW * (int)sizeof(T);
-  // s_fill: the next fill's sequence number; kBusy is or-ed in while a warp
-  // is choosing that fill's tile (one choice at a time, so dynamic tiles are
+  // s_fill: the next fill as 8 * round + stage (fill j = round * nstage +
+  // stage, so no division in the loop); kBusy is or-ed in while a warp is
+  // choosing that fill's tile (one choice at a time, so dynamic tiles are
   // taken in fill order); kNoMoreFills once a fill came back empty
   constexpr int kBusy = 1 << 29, kNoMoreFills = 1 << 30;
 
@@ -576,7 +593,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       mbar_init(&s_bar[k], 1);
       s_done[k] = 0;
     }
-    s_fill = p.nstage;
+    s_fill = 8;  // round 1, stage 0: warp 0 issues round 0
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (STATS) {
@@ -603,14 +620,14 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   // publishes its geometry (released by the mbarrier arrive) and, for a
   // claimed fill, hands the next fill on; the lanes issue the copies.  With no
   // tile left the stage completes empty and no further fill is claimed.
-  auto fill = [&](int j, int rs, bool claimed) {
+  auto fill = [&](int j, int rs, int next) {  // next: s_fill after a claimed fill, else -1
     TileGeom g{0, 0, -1};
     if (lane == 0) {
       const long long t = tile_of_fill(j);
       if (t >= 0) {
         g = tile_geom(p, t);
         s_geo[rs] = make_int4(g.xc, g.zg, g.y, 1);
-        if (claimed) *reinterpret_cast<volatile int*>(&s_fill) = j + 1;
+        if (next >= 0) *reinterpret_cast<volatile int*>(&s_fill) = next;
       } else {
         s_geo[rs] = make_int4(0, 0, -1, 0);
         *reinterpret_cast<volatile int*>(&s_fill) = kNoMoreFills;
@@ -632,7 +649,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   // faster (B300: FP32 122.7 -> 119.4 us without the barrier, FP16 115.5 ->
   // 123.9 us).
   if (warp == 0) {
-    for (int k = 0; k < p.nstage; k++) fill(k, k, false);
+    for (int k = 0; k < p.nstage; k++) fill(k, k, -1);
     if (sizeof(T) == 2) {
       const float v = controlled_gx(p, lane);
       if (lane == 0) s_gx = v;
@@ -650,15 +667,16 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
     if (lane == 0) {
       const int jn = *reinterpret_cast<volatile int*>(&s_fill);
       if (jn < kBusy) {
-        const unsigned need = (unsigned)(jn / p.nstage) * nwarps;
-        const unsigned done = *reinterpret_cast<volatile unsigned*>(&s_done[jn % p.nstage]);
+        const unsigned need = (unsigned)(jn >> 3) * nwarps;
+        const unsigned done = *reinterpret_cast<volatile unsigned*>(&s_done[jn & 7]);
         if (done >= need && atomicCAS(&s_fill, jn, jn | kBusy) == jn) j = jn;
       }
     }
     j = __shfl_sync(0xffffffffu, j, 0);
     if (j >= 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      fill(j, j % p.nstage, true);
+      const int k = j & 7, r = j >> 3;
+      fill(r * p.nstage + k, k, k + 1 == p.nstage ? (r + 1) * 8 : j + 1);
     }
   };
 
@@ -670,9 +688,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   int stat_xc = -1;
   const bool flush_on_chunk = p.nbins > 1 && p.nxc > 1;
 
-  for (int t = 0;; t++) {
-    const int st = t % p.nstage;
-    const uint32_t parity = (uint32_t)((t / p.nstage) & 1);
+  int st = 0;           // stage of this iteration's tile
+  uint32_t parity = 0;  // its mbarrier phase parity
+  for (;; st = (st + 1 == p.nstage) ? 0 : st + 1, parity ^= (st == 0)) {
     const unsigned char* stage = smem + st * stage_bytes;
 
     try_refill();
