@@ -688,9 +688,10 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   int stat_xc = -1;
   const bool flush_on_chunk = p.nbins > 1 && p.nxc > 1;
 
-  int st = 0;           // stage of this iteration's tile
-  uint32_t parity = 0;  // its mbarrier phase parity
-  for (;; st = (st + 1 == p.nstage) ? 0 : st + 1, parity ^= (st == 0)) {
+  int sp = 0;  // 8 * mbarrier phase parity + stage of this iteration's tile
+  for (;; sp = ((sp & 7) + 1 == p.nstage) ? ((sp & 8) ^ 8) : sp + 1) {
+    const int st = sp & 7;
+    const uint32_t parity = (uint32_t)sp >> 3;
     const unsigned char* stage = smem + st * stage_bytes;
 
     try_refill();
