@@ -149,6 +149,19 @@ lbm_status lbm_stats_reset(lbm_ctx* ctx, int32_t enable);
  * n must be >= 9*stats_xbins*ny.  *samples = time steps accumulated. */
 lbm_status lbm_stats(lbm_ctx* ctx, double* out, size_t n, int64_t* samples);
 
+/* Pipelined read-out of the same averages, for a caller that reads every
+ * step's result without idling the GPU: lbm_stats_begin enqueues, on the
+ * context's stream after the work already enqueued, one asynchronous copy of
+ * the accumulators and health flags into a pinned slot of the library (two
+ * slots; LBM_ERR_ARG when both hold a pending read-out) and returns at once;
+ * lbm_stats_end waits for the oldest pending read-out and fills `out` and
+ * `samples` exactly as lbm_stats would have at the point of the matching
+ * begin (LBM_ERR_ARG when none is pending).  A step enqueued between the two
+ * calls runs while the host waits.  Device-side errors (LBM_ERR_NAN,
+ * LBM_ERR_TIMEOUT) are reported by lbm_stats_end. */
+lbm_status lbm_stats_begin(lbm_ctx* ctx);
+lbm_status lbm_stats_end(lbm_ctx* ctx, double* out, size_t n, int64_t* samples);
+
 /* Global mass: sum over cells and directions of the stored populations, FP64. */
 lbm_status lbm_mass(lbm_ctx* ctx, double* out);
 

@@ -71,6 +71,8 @@ def lib():
         for name, args in [("lbm_set_stream", [vp, vp]), ("lbm_step", [vp, C.c_int32]),
                            ("lbm_sync", [vp]), ("lbm_stats_reset", [vp, C.c_int32]),
                            ("lbm_stats", [vp, _DP, C.c_size_t, C.POINTER(C.c_int64)]),
+                           ("lbm_stats_begin", [vp]),
+                           ("lbm_stats_end", [vp, _DP, C.c_size_t, C.POINTER(C.c_int64)]),
                            ("lbm_mass", [vp, _DP]), ("lbm_get_f", [vp, _DP, C.c_size_t]),
                            ("lbm_set_f", [vp, _DP, C.c_size_t]),
                            ("lbm_get_macro", [vp, _DP, _DP, C.c_size_t]),
@@ -181,6 +183,16 @@ def lbm_stats_reset(ctx, enable=True):
 def lbm_stats(ctx, out: np.ndarray):
     n = C.c_int64()
     _check(lib().lbm_stats(ctx, _dp(out), out.size, C.byref(n)), ctx, "lbm_stats")
+    return int(n.value)
+
+
+def lbm_stats_begin(ctx):
+    _check(lib().lbm_stats_begin(ctx), ctx, "lbm_stats_begin")
+
+
+def lbm_stats_end(ctx, out: np.ndarray):
+    n = C.c_int64()
+    _check(lib().lbm_stats_end(ctx, _dp(out), out.size, C.byref(n)), ctx, "lbm_stats_end")
     return int(n.value)
 
 
@@ -489,6 +501,19 @@ class Domain:
     def stats(self):
         out = np.zeros((9, self.case.stats_xbins, self.case.ny))
         n = lbm_stats(self.ctx, out)
+        return out, n
+
+    def stats_begin(self):
+        """Enqueue a read-out of the statistics after the work enqueued so far
+        (at most two pending)."""
+        lbm_stats_begin(self.ctx)
+
+    def stats_end(self, out=None):
+        """The oldest pending read-out, as stats() would have returned it at
+        the matching stats_begin()."""
+        if out is None:
+            out = np.zeros((9, self.case.stats_xbins, self.case.ny))
+        n = lbm_stats_end(self.ctx, out)
         return out, n
 
     def drive(self):

@@ -126,7 +126,11 @@ struct lbm_ctx {
   const lbm_mlp* mlp = nullptr;  // learned first-layer correction in use, if any
   float lam = 0.f;               // its velocity relaxation rate
   float* feat_buf = nullptr;     // staging buffer of lbm_features
-  unsigned char* readout = nullptr;  // pinned host copy of the statistics and health flags
+  unsigned char* readout = nullptr;  // pinned host copies of the statistics and health flags:
+                                     // slot 0 for lbm_stats, slots 1 and 2 for the pipelined read-out
+  cudaEvent_t rd_ev[2] = {nullptr, nullptr};  // completion of the pipelined copies
+  int64_t rd_samples[2] = {0, 0};             // steps accumulated when each copy was enqueued
+  int rd_first = 0, rd_pending = 0;           // oldest pending slot (0/1), pending count
 
   void* fbuf(int k) const { return ws + (size_t)k * L.f_bytes; }
   double* stats() const { return reinterpret_cast<double*>(ws + L.stats_off); }
@@ -572,36 +576,42 @@ lbm_status lbm_stats_reset(lbm_ctx* c, int32_t enable) {
   return LBM_OK;
 }
 
-lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
-  READY(c);
+namespace {
+
+size_t readout_bytes(const lbm_ctx* c) { return c->L.state_off + sizeof(DevState) - c->L.stats_off; }
+
+// pinned read-out slots (three, allocated on first use)
+lbm_status ensure_readout(lbm_ctx* c, const char* who) {
+  if (c->readout) return LBM_OK;
+  const size_t slot = align_up(readout_bytes(c), kAlign);
+  if (cudaMallocHost(&c->readout, 3 * slot) != cudaSuccess) {
+    cudaGetLastError();
+    c->readout = nullptr;
+    return fail(c, LBM_ERR_OOM, std::string(who) + ": cudaMallocHost of the readout buffer failed");
+  }
+  return LBM_OK;
+}
+
+unsigned char* readout_slot(const lbm_ctx* c, int k) {
+  return c->readout + (size_t)k * align_up(readout_bytes(c), kAlign);
+}
+
+// Health flags and the averages of one read-out slot.
+lbm_status finish_readout(lbm_ctx* c, const unsigned char* buf, int64_t nsamples, double* out,
+                          int64_t* samples) {
   const int ny = c->grid.ny, nb = c->nbins, nx = c->grid.nx;
   const size_t m = (size_t)nb * ny;
-  if (!out || n < 9 * m) return arg_error(c, "lbm_stats: output too small");
-  // one asynchronous copy of the statistics and the health flags (adjacent in
-  // the workspace) into pinned memory, then one wait on the context's stream
-  const size_t bytes = c->L.state_off + sizeof(DevState) - c->L.stats_off;
-  if (!c->readout) {
-    if (cudaMallocHost(&c->readout, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      c->readout = nullptr;
-      return fail(c, LBM_ERR_OOM, "lbm_stats: cudaMallocHost of the readout buffer failed");
-    }
-  }
-  CK(c, cudaMemcpyAsync(c->readout, c->ws + c->L.stats_off, bytes, cudaMemcpyDeviceToHost,
-                        c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
-  CK(c, cudaGetLastError());
-  const DevState* st = reinterpret_cast<const DevState*>(c->readout + (c->L.state_off - c->L.stats_off));
+  const DevState* st = reinterpret_cast<const DevState*>(buf + (c->L.state_off - c->L.stats_off));
   if (st->timeout_flag)
     return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
   if (st->nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density");
-  const double* acc = reinterpret_cast<const double*>(c->readout);
+  const double* acc = reinterpret_cast<const double*>(buf);
   std::vector<long long> width(nb, 0);
   for (int x = 0; x < nx; x++) width[(long long)x * nb / nx]++;
   for (int b = 0; b < nb; b++)
     for (int y = 0; y < ny; y++) {
       const size_t k = (size_t)b * ny + y;
-      const double cnt = (double)c->stats_samples * (double)c->grid.nz * (double)width[b];
+      const double cnt = (double)nsamples * (double)c->grid.nz * (double)width[b];
       const double inv = cnt > 0 ? 1.0 / cnt : 0.0;
       const double mu = acc[0 * m + k] * inv, mv = acc[1 * m + k] * inv, mw = acc[2 * m + k] * inv;
       out[0 * m + k] = mu;
@@ -614,8 +624,52 @@ lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
       out[7 * m + k] = acc[7 * m + k] * inv - mu * mw;
       out[8 * m + k] = acc[8 * m + k] * inv - mv * mw;
     }
-  if (samples) *samples = c->stats_samples;
+  if (samples) *samples = nsamples;
   return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_stats(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
+  READY(c);
+  if (!out || n < 9 * (size_t)c->nbins * c->grid.ny) return arg_error(c, "lbm_stats: output too small");
+  lbm_status s = ensure_readout(c, "lbm_stats");
+  if (s != LBM_OK) return s;
+  // one asynchronous copy of the statistics and the health flags (adjacent in
+  // the workspace) into pinned memory, then one wait on the context's stream
+  CK(c, cudaMemcpyAsync(readout_slot(c, 0), c->ws + c->L.stats_off, readout_bytes(c),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, cudaGetLastError());
+  return finish_readout(c, readout_slot(c, 0), c->stats_samples, out, samples);
+}
+
+lbm_status lbm_stats_begin(lbm_ctx* c) {
+  READY(c);
+  if (c->rd_pending == 2) return arg_error(c, "lbm_stats_begin: two read-outs already pending");
+  lbm_status s = ensure_readout(c, "lbm_stats_begin");
+  if (s != LBM_OK) return s;
+  const int k = (c->rd_first + c->rd_pending) & 1;
+  if (!c->rd_ev[k]) CK(c, cudaEventCreateWithFlags(&c->rd_ev[k], cudaEventDisableTiming));
+  CK(c, cudaMemcpyAsync(readout_slot(c, 1 + k), c->ws + c->L.stats_off, readout_bytes(c),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaEventRecord(c->rd_ev[k], c->stream));
+  c->rd_samples[k] = c->stats_samples;
+  c->rd_pending++;
+  return LBM_OK;
+}
+
+lbm_status lbm_stats_end(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
+  READY(c);
+  if (c->rd_pending == 0) return arg_error(c, "lbm_stats_end: no read-out pending");
+  if (!out || n < 9 * (size_t)c->nbins * c->grid.ny)
+    return arg_error(c, "lbm_stats_end: output too small");
+  const int k = c->rd_first;
+  CK(c, cudaEventSynchronize(c->rd_ev[k]));
+  CK(c, cudaGetLastError());
+  c->rd_first ^= 1;
+  c->rd_pending--;
+  return finish_readout(c, readout_slot(c, 1 + k), c->rd_samples[k], out, samples);
 }
 
 lbm_status lbm_mass(lbm_ctx* c, double* out) {
@@ -866,6 +920,8 @@ void lbm_destroy(lbm_ctx* c) {
   if (c->macro_buf) cudaFree(c->macro_buf);
   if (c->feat_buf) cudaFree(c->feat_buf);
   if (c->readout) cudaFreeHost(c->readout);
+  for (cudaEvent_t e : c->rd_ev)
+    if (e) cudaEventDestroy(e);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   delete c;
 }
