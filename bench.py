@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-canopy", action="store_true",
                     help="skip the 512x128x256 canopy leg (x-binned statistics)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--profile", metavar="NXxNYxNZ|ensemble|learned", default=None,
+    ap.add_argument("--profile", metavar="NXxNYxNZ|canopy|ensemble|learned", default=None,
                     help="run a few steps of the channel workload at this size (or of the "
                          "64-box ensemble, or of a 256x64x128 canopy domain with the learned "
                          "correction) and exit: the cases the ncu summaries under profiles/ "
@@ -69,9 +69,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(storage_name, cells):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled from the captured case to `cells`; None if the kernel changed since."""
+def measured_traffic(storage_name, cells, workload="channel"):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (the channel captures, or the canopy one), scaled from the captured case to
+    `cells`; None if the kernel changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as fh:
             t = json.load(fh)
@@ -79,7 +80,7 @@ def measured_traffic(storage_name, cells):
         return None
     if t.get("source_hash") != kernel_source_hash():
         return None
-    e = t.get("storage", {}).get(storage_name)
+    e = (t.get("storage", {}) if workload == "channel" else t.get(workload, {})).get(storage_name)
     if not e:
         return None
     return (e["dram_read_bytes"] + e["dram_write_bytes"]) * cells / e["cells"]
@@ -186,6 +187,7 @@ def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
 
     case = W.channel_les()
     d = P.Domain(case, storage)
+    d.mass0 = d.mass()  # FP64 global mass of the initial state (mass drift below)
     if with_stats:
         d.stats_reset(True)
     stream = d.stream
@@ -273,7 +275,8 @@ def time_canopy(P, W, steps, warmup, hbm):
         ach = P.BYTES_PER_LUP[st] * case.cells / (ms * 1e-3) / 1e9
         out[name] = {"value": round(case.cells / ms / 1e3, 1), "unit": "MLUPS", "ms_per_step": ms,
                      "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
-                                  "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None}}
+                                  "unit": "GB/s", "frac": round(ach / hbm, 4),
+                                  "traffic": measured_traffic(name, case.cells, "canopy")}}
     return out
 
 
@@ -345,6 +348,22 @@ def e2e_run(P, d, steps):
     return dt, d2h
 
 
+def cpu_baseline_single_thread(seconds):
+    """The same oracle sample in a child process with OMP_NUM_THREADS=1."""
+    import subprocess
+    import sys
+
+    code = ("import json, bench, workloads as W; "
+            f"print(json.dumps(bench.cpu_baseline(W.channel_les, {seconds!r})))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": out["value"], "unit": out["unit"], "cores": 1, "sample": out["sample"]}
+
+
 def cpu_baseline(case_factory, seconds):
     """The FP64 oracle, as it stands, on this host's cores: a bounded sample of
     the same workload (whole time steps of the full grid)."""
@@ -411,6 +430,9 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    m1 = d.mass()
+    res["mass"] = {"initial": d.mass0, "after_steps": d.steps_done(), "final": m1,
+                   "rel_drift": (m1 - d.mass0) / d.mass0}
     # end to end through the public API with host-side results every step
     e2e_steps = min(args.steps, 500)
     dt, d2h = e2e_run(P, d, e2e_steps)
@@ -453,6 +475,7 @@ def run_ours(args):
         res["learned"] = time_learned(P, W, min(args.steps, 100), max(min(args.warmup, 10), 3))
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(W.channel_les, args.cpu_seconds)
+        res["cpu_baseline"]["single_thread"] = cpu_baseline_single_thread(args.cpu_seconds / 3)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:
@@ -517,6 +540,14 @@ def run_profile_case(args):
         b.sync()
         b.close()
         print("profile case: 64-box ensemble, FP16-shifted: 6 steps done")
+        return
+    if args.profile == "canopy":
+        d = P.Domain(W.canopy_abl(512, 128, 128), P.STORAGE_NAMES[args.storage])
+        d.stats_reset(True)
+        d.step(6)
+        d.sync()
+        d.close()
+        print(f"profile case: canopy 512x128x128 {args.storage} with x-binned statistics: 6 steps")
         return
     if args.profile == "learned":
         d = P.Domain(W.canopy_abl(256, 64, 128, h=12.0, a=0.25, cd=0.15, canopy_x0=64, xbin=16))
