@@ -174,6 +174,16 @@ lbm_status lbm_set_f(lbm_ctx* ctx, const double* host_f, size_t n);
  * rho[z][y][x] (n = nx*ny*nz values) and u[3][z][y][x] (3n values). */
 lbm_status lbm_get_macro(lbm_ctx* ctx, double* rho, double* u, size_t n);
 
+/* Q-criterion of that velocity field, q[z][y][x] (n = nx*ny*nz values), the
+ * quantity whose iso-surfaces show vortical structures (Sec. 4, the
+ * turbulent-channel figure): Q = (|Omega|^2 - |S|^2)/2, S and Omega the symmetric and
+ * antisymmetric parts of the velocity gradient, differentiated with central
+ * differences (periodic wrap; one-sided at the first and last cell of a
+ * bounded direction; zero across a direction one cell wide).  FP32 on the
+ * device, returned as FP64.  Uses the same device field buffer as
+ * lbm_get_macro (allocated on first use). */
+lbm_status lbm_get_q(lbm_ctx* ctx, double* q, size_t n);
+
 /* Same output as lbm_get_macro, without allocating device memory.  The paper
  * has no counterpart: this serves callers that must not call cudaMalloc (a
  * fixed memory budget or pre-reserved pool, or code running while other work

@@ -77,6 +77,7 @@ def lib():
                            ("lbm_set_f", [vp, _DP, C.c_size_t]),
                            ("lbm_get_macro", [vp, _DP, _DP, C.c_size_t]),
                            ("lbm_get_macro_noalloc", [vp, _DP, _DP, C.c_size_t]),
+                           ("lbm_get_q", [vp, _DP, C.c_size_t]),
                            ("lbm_drive", [vp, _DP, _DP]), ("lbm_save", [vp, C.c_char_p]),
                            ("lbm_load", [vp, C.c_char_p])]:
             fn = getattr(L, name)
@@ -194,6 +195,10 @@ def lbm_stats_end(ctx, out: np.ndarray):
     n = C.c_int64()
     _check(lib().lbm_stats_end(ctx, _dp(out), out.size, C.byref(n)), ctx, "lbm_stats_end")
     return int(n.value)
+
+
+def lbm_get_q(ctx, q: np.ndarray):
+    _check(lib().lbm_get_q(ctx, _dp(q), q.size), ctx, "lbm_get_q")
 
 
 def lbm_mass(ctx):
@@ -491,6 +496,12 @@ class Domain:
         rho, u = np.zeros(self.shape), np.zeros((3,) + self.shape)
         lbm_get_macro(self.ctx, rho, u)
         return rho, u
+
+    def q_criterion(self):
+        """Q-criterion [z][y][x] of the velocity field the next step computes."""
+        q = np.zeros(self.shape)
+        lbm_get_q(self.ctx, q)
+        return q
 
     def mass(self):
         return lbm_mass(self.ctx)

@@ -19,6 +19,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
+#include "lbm_diag.cuh"
 #include "lbm_mlp.cuh"
 
 using namespace lbm;
@@ -753,6 +754,34 @@ lbm_status lbm_get_macro(lbm_ctx* c, double* rho, double* u, size_t n) {
   CK(c, cudaMemcpy(h.data(), c->macro_buf, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
   for (long long k = 0; k < c->cells; k++) rho[k] = h[k];
   for (long long k = 0; k < 3 * c->cells; k++) u[k] = h[c->cells + k];
+  return LBM_OK;
+}
+
+lbm_status lbm_get_q(lbm_ctx* c, double* q, size_t n) {
+  READY(c);
+  if (!q || n != (size_t)c->cells) return arg_error(c, "lbm_get_q: wrong size");
+  if (!c->macro_buf) {
+    if (cudaMalloc(&c->macro_buf, sizeof(float) * 4 * c->cells) != cudaSuccess) {
+      cudaGetLastError();
+      c->macro_buf = nullptr;
+      return fail(c, LBM_ERR_OOM, "lbm_get_q: cudaMalloc of the field buffer failed");
+    }
+  }
+  const StepParams p = make_params(c);
+  dispatch(c, [&](auto xt, auto s) {
+    launch_macro<decltype(xt)::value, decltype(s)::value>(c, p, c->macro_buf);
+  });
+  // Q into the density plane of the field buffer (the kernel reads the velocity planes only)
+  const lbm_grid& g = c->grid;
+  q_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->macro_buf + c->cells, c->macro_buf, g.nx,
+                                                   g.ny, g.nz, g.x_lo == LBM_BC_PERIODIC,
+                                                   g.y_lo == LBM_BC_PERIODIC);
+  CK(c, cudaGetLastError());
+  lbm_status s = check_device(c);
+  if (s != LBM_OK) return s;
+  std::vector<float> h((size_t)c->cells);
+  CK(c, cudaMemcpy(h.data(), c->macro_buf, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+  for (long long k = 0; k < c->cells; k++) q[k] = h[k];
   return LBM_OK;
 }
 
