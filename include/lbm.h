@@ -139,6 +139,16 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
 /* Wait for the context's stream and report device-side errors. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
+/* Test hook for the timeout path: in the next lbm_step (one step) block 0
+ * of the step kernel does not issue its `fill`-th tile fill (fills count
+ * from 0 per block; an index past the block's fills withholds nothing), so
+ * the waits on that stage can only run out.  Every device wait gives up
+ * after 2^18 polls of mbarrier.try_wait (about a second on a B300); the step
+ * then sets the timeout flag, the next synchronising call returns
+ * LBM_ERR_TIMEOUT (sticky), the kernel leaves no copy in flight and the
+ * device stays usable.  LBM_ERR_ARG for fill < 0. */
+lbm_status lbm_test_withhold_fill(lbm_ctx* ctx, int32_t fill);
+
 /* Zero the statistics accumulators; enable != 0 makes every following step
  * add its velocities to them (Sec. 4: averaged in time, then over x-z planes). */
 lbm_status lbm_stats_reset(lbm_ctx* ctx, int32_t enable);

@@ -78,6 +78,7 @@ def lib():
                            ("lbm_get_macro", [vp, _DP, _DP, C.c_size_t]),
                            ("lbm_get_macro_noalloc", [vp, _DP, _DP, C.c_size_t]),
                            ("lbm_get_q", [vp, _DP, C.c_size_t]),
+                           ("lbm_test_withhold_fill", [vp, C.c_int32]),
                            ("lbm_drive", [vp, _DP, _DP]), ("lbm_save", [vp, C.c_char_p]),
                            ("lbm_load", [vp, C.c_char_p])]:
             fn = getattr(L, name)
@@ -199,6 +200,10 @@ def lbm_stats_end(ctx, out: np.ndarray):
 
 def lbm_get_q(ctx, q: np.ndarray):
     _check(lib().lbm_get_q(ctx, _dp(q), q.size), ctx, "lbm_get_q")
+
+
+def lbm_test_withhold_fill(ctx, fill):
+    _check(lib().lbm_test_withhold_fill(ctx, fill), ctx, "lbm_test_withhold_fill")
 
 
 def lbm_mass(ctx):

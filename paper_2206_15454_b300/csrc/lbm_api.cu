@@ -118,6 +118,7 @@ struct lbm_ctx {
   int sm_count = 0, blocks_per_sm = 0;
   int last_grid = 0;          // blocks of the previous step launch (partials to sum)
   int nstage = 0;             // tiles in flight per block
+  int test_withhold = -1;     // lbm_test_withhold_fill: fill block 0 skips in the next step
   size_t stage_smem = 0;      // dynamic shared memory per block
   dim3 block;
   int nzg = 0;
@@ -241,6 +242,7 @@ StepParams make_params(const lbm_ctx* c) {
   p.nzg = c->nzg;
   p.ntiles = (long long)c->sh.nxc * c->nzg * g.ny;
   p.nstage = c->nstage;
+  p.withhold = c->test_withhold;
   // a share of the tiles in fixed contiguous runs per block, the rest handed
   // out one by one to whichever block is free (blocks of an SM do not run at
   // the same speed)
@@ -551,6 +553,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
       launch_step<decltype(xt)::value, decltype(s)::value>(c, p, c->stats_on);
     });
     CK(c, cudaGetLastError());
+    c->test_withhold = -1;  // a test hook acts on one step
     c->last_grid = step_grid(c);
     c->cur = 1 - c->cur;
     c->steps++;
@@ -561,6 +564,13 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
       CK(c, cudaGetLastError());
     }
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_test_withhold_fill(lbm_ctx* c, int32_t fill) {
+  READY(c);
+  if (fill < 0) return arg_error(c, "lbm_test_withhold_fill: fill < 0");
+  c->test_withhold = fill;
   return LBM_OK;
 }
 

@@ -132,6 +132,7 @@ struct StepParams {
   float t_in_inv, t_mid_inv;
   long long ntiles;
   int nstage;               // tiles in flight per block
+  int withhold;             // >= 0: block 0 never issues this fill (test of the timeout path)
   // work split of one domain: block b first walks the static run of tiles
   // [b * static_tiles, (b + 1) * static_tiles), then takes tiles one by one
   // from [gridDim.x * static_tiles, ntiles) through tile_ctr[ctr_slot]
@@ -465,7 +466,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     if (mbar_try(bar, parity)) return true;
   return false;
 }
-constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls (each may suspend ~us) before giving up
+// polls before a wait gives up and sets the timeout flag: a poll may suspend
+// for a few microseconds (B300: about 4.5 us), so about a second, against
+// waits of microseconds on the normal path
+constexpr uint32_t WAIT_LIMIT = 1u << 18;
 
 // Direction components packed two bits each (1: +1, 2: -1) and the y-mirror
 // five bits each, so lanes holding different directions run the same code.
@@ -574,6 +578,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   __shared__ __align__(8) uint64_t s_bar[8];
   __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
   __shared__ int s_fill;              // next fill to issue: 8 * round + stage
+  __shared__ int s_nfill;             // fills issued so far (their copies may be in flight)
   __shared__ int4 s_geo[8];           // (xc, zg, y, 1) of the tile each stage holds; y < 0: none
 
   const int tx = threadIdx.x;
@@ -594,6 +599,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       s_done[k] = 0;
     }
     s_fill = 8;  // round 1, stage 0: warp 0 issues round 0
+    s_nfill = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (STATS) {
@@ -623,6 +629,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   auto fill = [&](int j, int rs, int next) {  // next: s_fill after a claimed fill, else -1
     TileGeom g{0, 0, -1};
     if (lane == 0) {
+      s_nfill = j + 1;  // fills are issued in order
       const long long t = tile_of_fill(j);
       if (t >= 0) {
         g = tile_geom(p, t);
@@ -637,7 +644,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
     g.xc = __shfl_sync(0xffffffffu, g.xc, 0);
     g.zg = __shfl_sync(0xffffffffu, g.zg, 0);
     g.y = __shfl_sync(0xffffffffu, g.y, 0);
-    if (g.y >= 0) issue_tile<XT, S>(p, g, smem + rs * stage_bytes, &s_bar[rs], lane);
+    // (a withheld fill neither arrives nor copies: its stage's wait can only run out)
+    if (g.y >= 0 && !(j == p.withhold && blockIdx.x == 0))
+      issue_tile<XT, S>(p, g, smem + rs * stage_bytes, &s_bar[rs], lane);
   };
 
   if (tid == 0 && dynamic && blockIdx.x == 0) p.state->tile_ctr[1 - p.ctr_slot] = 0u;  // next step's
@@ -803,6 +812,17 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   }
   if (STATS && stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
   finish_step(p, ub_fix, bad, late, s_ub, lane, warp, tid, nthreads, part);
+  // Leave no copy in flight when the block ends: after a timed-out wait some
+  // issued fills were never consumed.  (On the normal path every issued fill
+  // has completed; the waits return at once.)  finish_step ended with a
+  // block barrier, so s_nfill is final.
+  if (tid == 0) {
+    const int nf = s_nfill;
+    for (int k = 0; k < p.nstage && k < nf; k++) {
+      const int uses = (nf - 1 - k) / p.nstage + 1;  // fills that went into stage k
+      mbar_wait(&s_bar[k], (uint32_t)((uses - 1) & 1), WAIT_LIMIT);
+    }
+  }
 }
 
 // One domain: block b walks its static run of tiles, then shares the rest.
