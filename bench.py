@@ -215,6 +215,17 @@ def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
     torch.cuda.synchronize()
     d.sync()
     per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # four more timed regions of the same K steps: run-to-run spread (the
+    # reported value stays the first region's)
+    repeats = [total_ms]
+    for _ in range(4):
+        t_begin.record(stream)
+        d.step(steps)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        repeats.append(t_begin.elapsed_time(t_end))
+    d.sync()
+    d.repeats_ms = repeats
     return d, case, total_ms, per_launch_ms
 
 
@@ -430,6 +441,12 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    d.repeats_ms = [max_over_ranks(ws, r) for r in d.repeats_ms]  # slowest rank per region
+    reps = sorted(r / args.steps for r in d.repeats_ms)
+    res["repeats"] = {"timed_regions": len(reps),
+                      "ms_per_step": [round(r / args.steps, 5) for r in d.repeats_ms],
+                      "best_value": round(cells * ws / (reps[0] * 1e-3) / 1e6, 1),
+                      "median_value": round(cells * ws / (reps[len(reps) // 2] * 1e-3) / 1e6, 1)}
     m1 = d.mass()
     res["mass"] = {"initial": d.mass0, "after_steps": d.steps_done(), "final": m1,
                    "rel_drift": (m1 - d.mass0) / d.mass0}
