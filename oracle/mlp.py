@@ -21,8 +21,8 @@ Pins: the forward pass, the gradient, Adam and the BF16 rounding are pinned
 against closed forms, central differences and known values.  The correction
 rule itself (correction_accel: how the four outputs become an acceleration)
 has no definition outside this project, so it is "parity unpinned": it is
-only checked for self-consistency, and the gain test against the coarsened
-finer run judges it.
+only checked for self-consistency; its measure is the gain test against the
+coarsened finer run.
 
 Parameters travel as one flat FP32/FP64 vector in this order:
 W1, b1, W2, b2, W3, b3, W4, b4 (row-major, rows = outputs), then

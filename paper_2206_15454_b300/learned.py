@@ -2,7 +2,7 @@
 
 The plain method (no wall function, no correction) is run on the coarse grid
 and on the same physical set-up at twice the resolution; the fine run's mean
-profiles, coarsened, are the judge of the coarse run.  The network learns, from
+profiles, coarsened, are the reference for the coarse run.  The network learns, from
 the coarse run's instantaneous column features, the time-averaged deficits of
 the coarse first cell (one cell high, wall half a cell below its centre) at
 that x-position:
