@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import paper_2206_15454_b300 as P
+from paper_2206_15454_b300 import post
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -262,10 +263,19 @@ def test_paper_abl_forest_cases_match_oracle(forest):
     with the three forest cases of Table tab:forest_cases, 100 steps."""
     case = W.abl_forest(forest, nx=40, ny=16, nz=12)
     d, o = pair(case)
-    d.step(100)
-    o.step(100)
+    d.step(60)
+    o.step(60)
+    d.stats_reset(True)
+    o.stats_reset(True)
+    d.step(40)
+    o.step(40)
     err = rel_l2(d.get_f(), o.get_f())
     assert err <= F32_TOL, (forest, err)
+    # the forest friction velocity of Sec. 5 (Reynolds stresses at y/h = 2)
+    h = 20.0 / (400.0 / case.ny)
+    us_d = post.friction_velocity(d.stats()[0], 2 * h)
+    us_o = post.friction_velocity(o.stats()[0], 2 * h)
+    assert us_o > 0 and abs(us_d - us_o) <= 0.02 * us_o, (forest, us_d, us_o)
 
 
 def test_paper_abl_forest_profiles_are_ordered():
