@@ -355,7 +355,7 @@ def e2e_run(P, d, steps):
         d.stats_end(out)
     d.stats_end(out)
     dt = time.perf_counter() - t0
-    d2h = out.nbytes + 16  # statistics + the device health flags (one pinned copy)
+    d2h = out.nbytes + 32  # statistics + the device health flags (one 32-byte block; one pinned copy)
     return dt, d2h
 
 

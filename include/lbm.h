@@ -67,7 +67,9 @@ typedef enum lbm_status {
                              or population shows as one within a step) */
     LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
     LBM_ERR_STATE = 6,    /* the context holds an earlier sticky error */
-    LBM_ERR_IO = 7        /* checkpoint file could not be written/read/verified */
+    LBM_ERR_IO = 7,       /* checkpoint file could not be written/read/verified */
+    LBM_ERR_BOUNDS = 8    /* checked builds (-DLBM_CHECK_BOUNDS) only: a bulk copy or store
+                             of the step fell outside its buffer and was skipped */
 } lbm_status;
 
 /* Boundary kinds.  Supported combinations: x periodic or INFLOW(x_lo) with

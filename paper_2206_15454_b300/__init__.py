@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_b300.so")
 
 Q = 19
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NAN, LBM_ERR_TIMEOUT, \
-    LBM_ERR_STATE, LBM_ERR_IO = range(8)
+    LBM_ERR_STATE, LBM_ERR_IO, LBM_ERR_BOUNDS = range(9)
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK, LBM_BC_FREESLIP, LBM_BC_EQUILIBRIUM, LBM_BC_INFLOW, \
     LBM_BC_OUTFLOW = range(6)
 LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = range(3)

@@ -28,20 +28,51 @@ def deps():
         os.path.join(ROOT, "include", "lbm.h"), os.path.abspath(__file__)]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB):
-        if os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in deps()):
-            return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+# The checked build: every bulk copy and global store of the step is verified
+# against its buffer (LBM_CHECK_BOUNDS); used by the tests, never by default.
+LIB_CHECKED = os.path.join(OUT_DIR, "liblbm_b300_checked.so")
+
+
+def _command(out: str, checked: bool, verbose: bool) -> list:
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
            "-prec-div=false", "-prec-sqrt=false",
            "-Xcompiler", "-fPIC", "-shared", "-cudart", "static",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB, *sources()]
+           "-I", os.path.join(ROOT, "include"), "-o", out, *sources()]
+    if checked:
+        cmd.insert(1, "-DLBM_CHECK_BOUNDS")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    return LIB
+    return cmd
+
+
+def _fresh(path: str) -> bool:
+    return os.path.exists(path) and os.path.getmtime(path) >= max(os.path.getmtime(p) for p in deps())
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Build the library (or, with checked=True, the checked build) in-tree."""
+    out = LIB_CHECKED if checked else LIB
+    if not force and _fresh(out):
+        return out
+    os.makedirs(OUT_DIR, exist_ok=True)
+    subprocess.run(_command(out, checked, verbose), check=True)
+    return out
+
+
+def build_all(force: bool = False) -> None:
+    """Both builds, compiled side by side."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    procs = [subprocess.Popen(_command(out, checked, False))
+             for out, checked in ((LIB, False), (LIB_CHECKED, True))
+             if force or not _fresh(out)]
+    for p in procs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, p.args)
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    if "--all" in sys.argv:
+        build_all(force="--force" in sys.argv)
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                    checked="--checked" in sys.argv))

@@ -396,6 +396,7 @@ lbm_status check_device(lbm_ctx* c) {
   CK(c, cudaGetLastError());
   DevState st;
   CK(c, cudaMemcpy(&st, c->state(), sizeof(st), cudaMemcpyDeviceToHost));
+  if (st.bounds_flag) return fail(c, LBM_ERR_BOUNDS, "an index left its buffer (checked build)");
   if (st.timeout_flag)
     return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
   if (st.nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density");
@@ -613,6 +614,7 @@ lbm_status finish_readout(lbm_ctx* c, const unsigned char* buf, int64_t nsamples
   const int ny = c->grid.ny, nb = c->nbins, nx = c->grid.nx;
   const size_t m = (size_t)nb * ny;
   const DevState* st = reinterpret_cast<const DevState*>(buf + (c->L.state_off - c->L.stats_off));
+  if (st->bounds_flag) return fail(c, LBM_ERR_BOUNDS, "an index left its buffer (checked build)");
   if (st->timeout_flag)
     return fail(c, LBM_ERR_TIMEOUT, "a device wait gave up after its iteration limit");
   if (st->nan_flag) return fail(c, LBM_ERR_NAN, "a cell produced a non-finite density");
@@ -980,6 +982,7 @@ const char* lbm_status_string(int32_t s) {
     case LBM_ERR_TIMEOUT: return "device wait timed out";
     case LBM_ERR_STATE: return "context holds an earlier error";
     case LBM_ERR_IO: return "checkpoint I/O error";
+    case LBM_ERR_BOUNDS: return "index out of its buffer (checked build)";
     default: return "unknown status";
   }
 }

@@ -76,7 +76,24 @@ struct DevState {
   unsigned int nan_flag;      // set when a cell produced a non-finite value
   unsigned int timeout_flag;  // set when a bounded device wait gave up
   unsigned int tile_ctr[2];   // dynamic tile counters, one per step parity
+  unsigned int bounds_flag;   // checked builds (LBM_CHECK_BOUNDS): an index left its buffer
+  unsigned int pad[3];
 };
+
+// Checked builds verify every bulk copy and every global store of the step
+// against the buffer it addresses; a violation sets bounds_flag and skips the
+// access (a skipped copy leaves its stage's wait to run out).  Off by default.
+#ifdef LBM_CHECK_BOUNDS
+constexpr bool kCheckBounds = true;
+#else
+constexpr bool kCheckBounds = false;
+#endif
+__device__ __forceinline__ bool in_range(long long lo, long long len, long long size,
+                                         DevState* st) {
+  if (lo >= 0 && len >= 0 && lo + len <= size) return true;
+  atomicOr(&st->bounds_flag, 1u);
+  return false;
+}
 
 constexpr int MAX_BLOCKS = 4096;  // per-block bulk-velocity partials per slot
 constexpr int MAX_XBINS = 64;
@@ -547,6 +564,14 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
     const T* src = base + (long long)((ys * p.nz + zs) * p.nxc + g.xc) * Gm::ROW + (long long)q * Gm::XTP;
     T* dst = reinterpret_cast<T*>(stage) + (r * NQ + i) * St::SROW + H;
     const int lo = dxi == 1 ? -H : 0, len = nal + (dxi != 0 ? H : 0);
+    if (kCheckBounds) {
+      const long long set = (long long)p.ny * p.nz * p.nxc * Gm::ROW;  // elements of a set
+      const long long so = (src + lo) - static_cast<const T*>(p.src);
+      const long long dofs = (dst + lo) - reinterpret_cast<T*>(stage);
+      if (!in_range(so, len, set, p.state) ||
+          !in_range(dofs, len, (long long)ry * NQ * St::SROW, p.state))
+        continue;
+    }
     bulk_g2s(dst + lo, src + lo, (uint32_t)len * sizeof(T), bar);
   }
 }
@@ -786,6 +811,16 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         }
       }
       collide(f, m, p.tau0, p.c18, [&](int i, float v) {
+        if (kCheckBounds) {
+          const long long set = (long long)p.ny * p.nz * p.nxc * Gm::ROW;
+          T* const d0 = static_cast<T*>(p.dst);
+          if (in_range(out + i * Gm::XTP - d0, 1, set, p.state)) Store<S>::st(out + i * Gm::XTP, v);
+          if (cx(i) == 1 && gr && in_range(gr + i * Gm::XTP - d0, 1, set, p.state))
+            Store<S>::st(gr + i * Gm::XTP, v);
+          if (cx(i) == -1 && gl && in_range(gl + i * Gm::XTP - d0, 1, set, p.state))
+            Store<S>::st(gl + i * Gm::XTP, v);
+          return;
+        }
         Store<S>::st(out + i * Gm::XTP, v);
         if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
         if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
@@ -796,7 +831,10 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         // taken from the line it just stored
 #pragma unroll
         for (int i = 0; i < NQ; i++)
-          if (cx(i) == -1) out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
+          if (cx(i) == -1 &&
+              (!kCheckBounds || in_range(out + 1 + i * Gm::XTP - static_cast<T*>(p.dst), 1,
+                                         (long long)p.ny * p.nz * p.nxc * Gm::ROW, p.state)))
+            out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
       }
       ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
       // health: a non-finite density (a non-finite velocity or population

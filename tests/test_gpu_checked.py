@@ -1,0 +1,68 @@
+"""The checked build (LBM_CHECK_BOUNDS: every bulk copy and global store of
+the step verified against its buffer) on every small boundary combination,
+ragged rows, chunked rows, a one-cell outflow chunk, 16-bit storage, an
+ensemble and x-binned statistics: no index leaves its buffer and the results
+still match the FP64 oracle.  Runs in a child process, which loads the checked
+library instead of the default one."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from paper_2206_15454_b300 import build as B
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r'''
+import sys
+import numpy as np
+import paper_2206_15454_b300 as P
+import workloads as W
+import oracle
+P.LIB_PATH = sys.argv[1]
+cases = W.small_cases() + [
+    W.Case("tiny_periodic", 1, 1, 1, bc_y=(W.PERIODIC, W.PERIODIC), tau0=0.7, init_perturb=0.03, seed=9),
+    W.poiseuille(1, 32, 1).replace(name="column"),
+    W.channel_les(300, 9, 5).replace(name="two_x_chunks"),
+    W.canopy_abl(257, 9, 5, h=3.0, canopy_x0=60, xbin=64).replace(name="outflow_one_cell_chunk"),
+    W.canopy_abl(600, 12, 6, h=4.0, canopy_x0=100, xbin=60).replace(name="xbinned_three_chunks"),
+]
+worst = 0.0
+for c in cases:
+    for st in (P.LBM_F32, P.LBM_F16_SHIFTED):
+        d, o = P.Domain(c, st), oracle.Oracle(c)
+        d.stats_reset(True)
+        o.stats_reset(True)
+        d.step(12)
+        o.step(12)
+        d.stats()
+        a, b = d.get_f(), o.get_f()
+        err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        bound = 1e-6 if st == P.LBM_F32 else 5e-3
+        assert err <= bound, (c.name, st, err)
+        worst = max(worst, err) if st == P.LBM_F32 else worst
+        d.close()
+        o.close()
+boxes = W.ensemble_boxes(n_boxes=5, ny=16, nz=12, nx_range=(40, 150), seed=77)
+bt = P.Batch(boxes, P.LBM_F16_SHIFTED)
+bt.step(6)
+bt.sync()
+for i, c in enumerate(boxes):
+    alone = P.Domain(c, P.LBM_F16_SHIFTED)
+    alone.step(6)
+    assert np.array_equal(bt.box(i).get_f(), alone.get_f()), c.name
+    alone.close()
+bt.close()
+print("checked build ok; worst FP32 rel L2", worst)
+'''
+
+
+def test_checked_build_keeps_every_index_in_its_buffer():
+    lib = B.build(checked=True)
+    r = subprocess.run([sys.executable, "-c", CHILD, lib], cwd=ROOT, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert "checked build ok" in r.stdout
