@@ -57,16 +57,26 @@ def parse():
     return ap.parse_args()
 
 
-def kernel_source_hash():
-    """Hash of the step kernel's source (lbm_device.cuh: the kernel, its tile
-    loop and launch-independent constants), to tell whether the profiles/
-    counters still apply."""
+def code_tokens(text: str) -> str:
+    """C/C++ source without its comments and with whitespace collapsed: what
+    the compiler sees (string literals in this file hold no comment markers)."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_source_hash(text=None):
+    """Hash of the step kernel's code (lbm_device.cuh: the kernel, its tile
+    loop and launch-independent constants; comments and layout do not count),
+    to tell whether the profiles/ counters still apply."""
     import hashlib
 
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2206_15454_b300", "csrc", "lbm_device.cuh"), "rb") as fh:
-        h.update(b"lbm_device.cuh" + fh.read())
-    return h.hexdigest()[:16]
+    if text is None:
+        with open(os.path.join(ROOT, "paper_2206_15454_b300", "csrc", "lbm_device.cuh")) as fh:
+            text = fh.read()
+    return hashlib.sha256(b"lbm_device.cuh" + code_tokens(text).encode()).hexdigest()[:16]
 
 
 def measured_traffic(storage_name, cells, workload="channel"):

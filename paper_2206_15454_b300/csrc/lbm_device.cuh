@@ -588,6 +588,12 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
 // first warp that looks, at the top of its iteration or while it waits for
 // data, so the copies are issued by a warp with time to spare and no
 // block-wide barrier sits in the loop.
+// Invariant: fills choose their tiles strictly in fill order (warp 0 issues
+// the first round in order before any claim can succeed; later fills are
+// claimed one at a time), so once a fill comes back empty no later stage holds
+// a tile and the consumers may leave at the first empty stage with no copy in
+// flight.  (Issuing prologue fills from several warps at once broke this and
+// let a block end with copies still landing in its shared memory.)
 template <int XT, int S, bool STATS>
 __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part,
                                            bool dynamic) {
