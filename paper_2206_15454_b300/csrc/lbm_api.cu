@@ -27,9 +27,8 @@ using namespace lbm;
 namespace {
 
 constexpr size_t kAlign = 256;
-#ifndef LBM_STATIC_PERCENT
-#define LBM_STATIC_PERCENT 90
-#endif
+// LBM_STATIC_PERCENT (for experiments) fixes the static share of every step's
+// tiles; by default it follows the run length (static_percent below)
 constexpr int kMassBlocks = 1024;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -199,8 +198,24 @@ void feq_shift(const double u[3], double out[NQ]) {
   }
 }
 
-// Percentage of a step's tiles that blocks take in their fixed runs.
-constexpr long long kStaticPercent = LBM_STATIC_PERCENT;
+// Share of a step's tiles handed out as fixed contiguous runs, the rest taken one
+// by one by whichever block is free.  The three blocks of an SM do not run at
+// the same speed (the first scheduled is ~15 % faster), so long runs need a
+// dynamic share of about that size; short runs pay more for dynamic tiles
+// than the imbalance costs them; 16-bit storage (shorter tiles in time)
+// reaches that point sooner.  B300, ms per step at 90 % / 85 %: 256x128x128
+// channel (37 tiles per block) FP32 0.1185 / 0.1228, FP16 0.1128 / 0.1162;
+// 512x128x256 canopy (148) FP32 0.4530 / 0.4562, FP16 0.4295 / 0.4180;
+// 1024x256x512 canopy (1180) FP32 3.54 / 3.36.
+long long static_percent(long long tiles_per_block, size_t elem) {
+#ifdef LBM_STATIC_PERCENT
+  (void)tiles_per_block;
+  (void)elem;
+  return LBM_STATIC_PERCENT;
+#else
+  return tiles_per_block > (elem == 2 ? 100 : 256) ? 85 : 90;
+#endif
+}
 
 int step_grid(const lbm_ctx* c) {
   const long long ntiles = (long long)c->sh.nxc * c->nzg * c->grid.ny;
@@ -246,7 +261,11 @@ StepParams make_params(const lbm_ctx* c) {
   // a share of the tiles in fixed contiguous runs per block, the rest handed
   // out one by one to whichever block is free (blocks of an SM do not run at
   // the same speed)
-  p.static_tiles = (int)(p.ntiles * kStaticPercent / 100 / step_grid(c));
+  {
+    const long long grid = step_grid(c);
+    p.static_tiles =
+        (int)(p.ntiles * static_percent(p.ntiles / grid, elem_bytes(c->storage)) / 100 / grid);
+  }
   p.ctr_slot = (int)(c->steps & 1);
   p.stats = c->stats();
   p.nbins = c->nbins;
