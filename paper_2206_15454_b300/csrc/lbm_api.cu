@@ -203,17 +203,19 @@ void feq_shift(const double u[3], double out[NQ]) {
 // the same speed (the first scheduled is ~15 % faster), so long runs need a
 // dynamic share of about that size; short runs pay more for dynamic tiles
 // than the imbalance costs them; 16-bit storage (shorter tiles in time)
-// reaches that point sooner.  B300, ms per step at 90 % / 85 %: 256x128x128
-// channel (37 tiles per block) FP32 0.1185 / 0.1228, FP16 0.1128 / 0.1162;
-// 512x128x256 canopy (148) FP32 0.4530 / 0.4562, FP16 0.4295 / 0.4180;
-// 1024x256x512 canopy (1180) FP32 3.54 / 3.36.
+// reaches that point sooner.  B300, ms per step at 92 / 90 / 88 / 85 %:
+// 256x128x128 channel (37 tiles per block) FP32 0.1186 / 0.1185 / 0.1200 /
+// 0.1228, FP16 0.1129 / 0.1128 / 0.1146 / 0.1162; 512x128x256 canopy (148)
+// FP32 0.4607 / 0.4530 / 0.4495 / 0.4562, FP16 0.4373 / 0.4295 / 0.4230 /
+// 0.4180; 1024x256x512 canopy (1180) FP32 at 90 / 85 %: 3.54 / 3.36.
 long long static_percent(long long tiles_per_block, size_t elem) {
 #ifdef LBM_STATIC_PERCENT
   (void)tiles_per_block;
   (void)elem;
   return LBM_STATIC_PERCENT;
 #else
-  return tiles_per_block > (elem == 2 ? 100 : 256) ? 85 : 90;
+  if (tiles_per_block <= 64) return 90;
+  return (elem == 2 || tiles_per_block > 256) ? 85 : 88;
 #endif
 }
 
