@@ -481,6 +481,8 @@ def run_ours(args):
         for name in ("f16s", "bf16s"):
             st = P.STORAGE_NAMES[name]
             dh, _, tot, lms = time_storage(P, W, st, args.steps, args.warmup, ws)
+            mh = dh.mass()
+            drift = {"after_steps": dh.steps_done(), "rel_drift": (mh - dh.mass0) / dh.mass0}
             dh.close()
             tot = max_over_ranks(ws, tot)
             ach = P.BYTES_PER_LUP[st] * cells / (tot / args.steps * 1e-3) / 1e9
@@ -493,7 +495,7 @@ def run_ours(args):
                          "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
                                       "unit": "GB/s", "frac": round(ach / hbm, 4),
                                       "traffic": measured_traffic(name, cells)},
-                         "rel_l2_f_vs_f32_after_100_steps": err}
+                         "rel_l2_f_vs_f32_after_100_steps": err, "mass": drift}
     if not args.no_canopy:
         res["canopy"] = time_canopy(P, W, min(args.steps, 500), max(args.warmup, 3), hbm)
     if not args.no_ensemble:
