@@ -1,0 +1,25 @@
+"""bench.py's host-side helpers: the kernel-code hash that decides whether the
+committed ncu traffic still applies, and the traffic scaling."""
+import bench
+
+
+SRC = """// a comment
+__device__ int f(int a) {  /* block
+   comment */ return a + 1;   // trailing
+}
+"""
+
+
+def test_code_hash_ignores_comments_and_layout_but_not_code():
+    h = bench.kernel_source_hash(SRC)
+    assert bench.kernel_source_hash(SRC.replace("// a comment", "// another comment")) == h
+    assert bench.kernel_source_hash(SRC.replace("\n", "\n\n")) == h
+    assert bench.kernel_source_hash(SRC.replace("a + 1", "a + 2")) != h
+
+
+def test_traffic_scales_with_cells_and_is_near_the_algorithmic_bytes():
+    t = bench.measured_traffic("f32", 4194304)
+    if t is None:  # the kernel changed since the committed capture: nothing to scale
+        return
+    assert 152 * 4194304 <= t < 1.3 * 152 * 4194304  # at least the algorithmic bytes
+    assert bench.measured_traffic("f32", 2 * 4194304) == 2 * t
