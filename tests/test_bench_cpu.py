@@ -21,5 +21,7 @@ def test_traffic_scales_with_cells_and_is_near_the_algorithmic_bytes():
     t = bench.measured_traffic("f32", 4194304)
     if t is None:  # the kernel changed since the committed capture: nothing to scale
         return
-    assert 152 * 4194304 <= t < 1.3 * 152 * 4194304  # at least the algorithmic bytes
+    # one captured launch: reads above the algorithmic half (ghost blocks), writes
+    # below it (the tail of the writes is still in L2 when the launch ends)
+    assert 0.8 * 152 * 4194304 < t < 1.2 * 152 * 4194304
     assert bench.measured_traffic("f32", 2 * 4194304) == 2 * t
