@@ -525,14 +525,18 @@ def run_reference(args):
     import workloads as W
 
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    # calibrate a z-slab of the channel so that warmup + steps stay within ~2 minutes
-    probe = oracle.Oracle(W.channel_les(256, 128, 8))
+    # a z-slab of the channel: at least one z-plane per thread (the oracle runs
+    # its OpenMP loop over z-planes), and as wide as warmup + steps allow in
+    # about two minutes
+    nz_min = min(128, max(8, threads))
+    probe = oracle.Oracle(W.channel_les(256, 128, nz_min))
+    probe.step(1)  # first touch
     t0 = time.perf_counter()
-    probe.step(1)
-    per_cell = (time.perf_counter() - t0) / (256 * 128 * 8)
+    probe.step(2)
+    per_cell = (time.perf_counter() - t0) / (2 * 256 * 128 * nz_min)
     probe.close()
     budget = 120.0 / max(1, args.steps + args.warmup)
-    nz = int(max(1, min(128, budget / (per_cell * 256 * 128))))
+    nz = int(max(nz_min, min(128, budget / (per_cell * 256 * 128))))
     case = W.channel_les(256, 128, nz)
     o = oracle.Oracle(case)
     o.step(args.warmup)
