@@ -31,6 +31,8 @@ class OlbmParams(C.Structure):
         ("u_top", C.c_double * 3),
         ("stats_xbins", C.c_int32), ("pad0", C.c_int32),
         ("seed", C.c_uint64), ("init_perturb", C.c_double),
+        ("drag_streamwise_only", C.c_int32), ("forcing_scheme", C.c_int32),
+        ("sgs_rho_power", C.c_int32), ("pad1", C.c_int32),
     ]
 
 
@@ -69,6 +71,12 @@ def lib():
         _lib.olbm_canopy_velocity.argtypes = [dp, C.c_double, dp]
         _lib.olbm_collide_cell.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double, dp,
                                            dp, dp]
+        _lib.olbm_canopy_velocity_x.argtypes = [dp, C.c_double, dp]
+        _lib.olbm_tau_total_p.restype = C.c_double
+        _lib.olbm_tau_total_p.argtypes = [C.c_double, C.c_double, C.c_double, dp, C.c_int]
+        _lib.olbm_edm_force.argtypes = [C.c_double, dp, dp, dp]
+        _lib.olbm_collide_cell_model.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double,
+                                                 C.c_int, C.c_int, C.c_int, dp, dp, dp]
         _lib.olbm_splitmix64.restype = C.c_uint64
         _lib.olbm_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         _lib.olbm_uniform.restype = C.c_double
@@ -120,6 +128,34 @@ def canopy_velocity(v, k):
     return u
 
 
+def canopy_velocity_x(v, k):
+    v = _vec(v, 3)
+    u = np.zeros(3)
+    lib().olbm_canopy_velocity_x(_dp(v), float(k), _dp(u))
+    return u
+
+
+def tau_total_p(tau0, cs, rho, pineq6, p):
+    q = _vec(pineq6, 6)
+    return lib().olbm_tau_total_p(float(tau0), float(cs), float(rho), _dp(q), int(p))
+
+
+def edm_force(rho, u, g):
+    u, g = _vec(u, 3), _vec(g, 3)
+    out = np.zeros(19)
+    lib().olbm_edm_force(float(rho), _dp(u), _dp(g), _dp(out))
+    return out
+
+
+def collide_cell_model(fin, g_drive, k, tau0, cs, drag_x_only=0, scheme=0, rho_power=1):
+    fin, g = _vec(fin, 19), _vec(g_drive, 3)
+    fout, rho, u = np.zeros(19), np.zeros(1), np.zeros(3)
+    lib().olbm_collide_cell_model(_dp(fin), _dp(g), float(k), float(tau0), float(cs),
+                                  int(drag_x_only), int(scheme), int(rho_power), _dp(fout),
+                                  _dp(rho), _dp(u))
+    return fout, float(rho[0]), u
+
+
 def collide_cell(fin, g_drive, k, tau0, cs):
     fin, g = _vec(fin, 19), _vec(g_drive, 3)
     fout, rho, u = np.zeros(19), np.zeros(1), np.zeros(3)
@@ -155,6 +191,9 @@ class Oracle:
         p.u_top[:] = list(case.u_top)
         p.stats_xbins = case.stats_xbins
         p.seed, p.init_perturb = case.seed, case.init_perturb
+        p.drag_streamwise_only = case.drag_streamwise_only
+        p.forcing_scheme = case.forcing_scheme
+        p.sgs_rho_power = case.sgs_rho_power
         self.case = case
         self.shape = (case.nz, case.ny, case.nx)
         self.n = case.nx * case.ny * case.nz

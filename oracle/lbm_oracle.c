@@ -23,7 +23,10 @@
  * local tau_total; C_smag = C_s^2 with filter width 1; tau_total carries
  * 1/rho under the root (the form that follows from Eq. strain); Pi_neq is
  * built from post-streaming populations and f_eq at the force-corrected
- * velocity; the canopy drag acts on the full velocity vector.
+ * velocity; the canopy drag acts on the full velocity vector.  Variants
+ * (olbm_params): the drag on the streamwise component only, exact-difference
+ * forcing (Kupershtokh) instead of Guo's, Q^1/2 / rho^2 under the root of
+ * tau_total (the tau_total equation as printed).
  */
 #include "lbm_oracle.h"
 
@@ -134,11 +137,20 @@ void olbm_guo(double tau, const double u[3], const double F[3], double Fi[19])
  * C_smag = C_s^2, filter width 1.  pineq = (xx, yy, zz, xy, xz, yz). */
 double olbm_tau_total(double tau0, double cs, double rho, const double pineq[6])
 {
+    return olbm_tau_total_p(tau0, cs, rho, pineq, 1);
+}
+
+/* The same with Q^(1/2) / rho^p under the root: p = 1 follows from Eq. strain
+ * solved for tau; p = 2 is the tau_total equation of Sec. 2.2 as printed
+ * ((tau0 rho c)^2 under the root, divided by 2 rho c, c = 1). */
+double olbm_tau_total_p(double tau0, double cs, double rho, const double pineq[6], int p)
+{
     double qq = pineq[0] * pineq[0] + pineq[1] * pineq[1] + pineq[2] * pineq[2] +
                 2.0 * (pineq[3] * pineq[3] + pineq[4] * pineq[4] + pineq[5] * pineq[5]);
     double q12 = sqrt(qq);
     double csmag = cs * cs;
-    return 0.5 * (tau0 + sqrt(tau0 * tau0 + 18.0 * sqrt(2.0) * csmag * q12 / rho));
+    double rp = (p == 2) ? rho * rho : rho;
+    return 0.5 * (tau0 + sqrt(tau0 * tau0 + 18.0 * sqrt(2.0) * csmag * q12 / rp));
 }
 
 /* Forest cell (Algorithm 1, Eqs. forestForce and momentum): the velocity u
@@ -153,9 +165,52 @@ void olbm_canopy_velocity(const double v[3], double k, double u[3])
     for (int a = 0; a < 3; a++) u[a] = scale * v[a];
 }
 
-void olbm_collide_cell(const double fin[19], const double g_drive[3], double k,
-                       double tau0, double cs, double fout[19],
-                       double* rho_out, double u_out[3])
+/* Streamwise-only forest drag (Eq. forestForce read as acting on the
+ * streamwise velocity component alone): g_c = (-k |u| u_x, 0, 0).  With
+ * u = v + g_c / 2, the cross-stream components are those of v and u_x solves
+ * phi(u_x) = u_x (1 + (k/2) sqrt(u_x^2 + s^2)) - v_x = 0, s^2 = v_y^2 + v_z^2.
+ * phi is increasing and changes sign between 0 and v_x, so bisection on that
+ * interval finds the root; it runs until the interval stops shrinking. */
+void olbm_canopy_velocity_x(const double v[3], double k, double u[3])
+{
+    double s2 = v[1] * v[1] + v[2] * v[2];
+    double lo = 0.0, hi = fabs(v[0]);
+    for (int it = 0; it < 2000; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double phi = mid * (1.0 + 0.5 * k * sqrt(mid * mid + s2)) - fabs(v[0]);
+        if (phi > 0.0) hi = mid;
+        else lo = mid;
+    }
+    double ux = 0.5 * (lo + hi);
+    u[0] = v[0] < 0.0 ? -ux : ux;
+    u[1] = v[1];
+    u[2] = v[2];
+}
+
+/* Exact-difference forcing (Kupershtokh): the force enters as the change of
+ * the equilibrium when the velocity is raised by g (one time step of the
+ * acceleration), f_eq(rho, u + g) - f_eq(rho, u). */
+void olbm_edm_force(double rho, const double u[3], const double g[3], double Fi[19])
+{
+    double ug[3] = {u[0] + g[0], u[1] + g[1], u[2] + g[2]};
+    double a[Q], b[Q];
+    olbm_feq(rho, ug, a);
+    olbm_feq(rho, u, b);
+    for (int i = 0; i < Q; i++) Fi[i] = a[i] - b[i];
+}
+
+/* One collision with the model variants.  Both forcing schemes share the
+ * physical velocity: u solves rho u = m + rho g_total / 2 (Eq. momentum) with
+ * the drag in g_total.  Guo (Eq. bodyforce) relaxes towards f_eq(rho, u);
+ * the exact-difference scheme relaxes towards f_eq(rho, u_b) at the bare
+ * velocity u_b = m / rho and adds f_eq(rho, u_b + g_total) - f_eq(rho, u_b);
+ * Pi_neq and tau_total are taken against the equilibrium the scheme relaxes
+ * towards. */
+void olbm_collide_cell_model(const double fin[19], const double g_drive[3], double k,
+                             double tau0, double cs, int drag_x_only, int scheme,
+                             int rho_power, double fout[19], double* rho_out,
+                             double u_out[3])
 {
     /* Eq. density and the first moment */
     double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
@@ -163,17 +218,25 @@ void olbm_collide_cell(const double fin[19], const double g_drive[3], double k,
         rho += fin[i];
         for (int a = 0; a < 3; a++) m[a] += fin[i] * CV[i][a];
     }
-    /* Eq. momentum with the driving force, then the forest correction */
+    /* Eq. momentum with the driving force, then the forest correction
+     * (Algorithm 1; drag of Eq. forestForce) */
     double v[3], u[3];
     for (int a = 0; a < 3; a++) v[a] = (m[a] + 0.5 * rho * g_drive[a]) / rho;
-    olbm_canopy_velocity(v, k, u);
+    if (drag_x_only) olbm_canopy_velocity_x(v, k, u);
+    else olbm_canopy_velocity(v, k, u);
     double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    double F[3];
-    for (int a = 0; a < 3; a++) F[a] = rho * (g_drive[a] - k * un * u[a]);
+    double g[3];
+    for (int a = 0; a < 3; a++) g[a] = g_drive[a];
+    if (drag_x_only) g[0] -= k * un * u[0];
+    else
+        for (int a = 0; a < 3; a++) g[a] -= k * un * u[a];
 
-    /* Eq. local_eq and the non-equilibrium momentum flux (Eq. tensor) */
+    /* Eq. local_eq at the velocity the scheme relaxes towards, and the
+     * non-equilibrium momentum flux (Eq. tensor) */
+    double urel[3];
+    for (int a = 0; a < 3; a++) urel[a] = (scheme == OLBM_EXACT_DIFFERENCE) ? m[a] / rho : u[a];
     double feq[Q];
-    olbm_feq(rho, u, feq);
+    olbm_feq(rho, urel, feq);
     double pineq[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < Q; i++) {
         double d = fin[i] - feq[i];
@@ -184,15 +247,26 @@ void olbm_collide_cell(const double fin[19], const double g_drive[3], double k,
         pineq[4] += CV[i][0] * CV[i][2] * d;
         pineq[5] += CV[i][1] * CV[i][2] * d;
     }
-    double tau = olbm_tau_total(tau0, cs, rho, pineq);
-
-    /* Eqs. lbe + bgk (relaxation towards f_eq) + bodyforce */
+    double tau = olbm_tau_total_p(tau0, cs, rho, pineq, rho_power);
+    /* Eqs. lbe + bgk (relaxation towards f_eq) plus the forcing term */
     double Fi[Q];
-    olbm_guo(tau, u, F, Fi);
+    if (scheme == OLBM_EXACT_DIFFERENCE) {
+        olbm_edm_force(rho, urel, g, Fi);
+    } else {
+        double F[3] = {rho * g[0], rho * g[1], rho * g[2]};
+        olbm_guo(tau, u, F, Fi);
+    }
     for (int i = 0; i < Q; i++) fout[i] = fin[i] - (fin[i] - feq[i]) / tau + Fi[i];
-
     *rho_out = rho;
     for (int a = 0; a < 3; a++) u_out[a] = u[a];
+}
+
+/* The default model: vector drag, Guo forcing, Q^1/2 / rho in tau_total. */
+void olbm_collide_cell(const double fin[19], const double g_drive[3], double k,
+                       double tau0, double cs, double fout[19],
+                       double* rho_out, double u_out[3])
+{
+    olbm_collide_cell_model(fin, g_drive, k, tau0, cs, 0, OLBM_GUO, 1, fout, rho_out, u_out);
 }
 
 uint64_t olbm_splitmix64(uint64_t seed, uint64_t n)
@@ -272,6 +346,15 @@ static void drive_for_next_step(const olbm* s, double g[3])
         g[0] = s->p.g[0] + s->p.ctrl_gain * (s->p.u_bulk_target - s->ub_last);
 }
 
+/* The collision of the domain's model (variants from the parameters). */
+static void collide(const olbm* s, const double fin[Q], const double g[3], double k,
+                    double fout[Q], double* rho, double u[3])
+{
+    const olbm_params* p = &s->p;
+    olbm_collide_cell_model(fin, g, k, p->tau0, p->cs, p->drag_streamwise_only,
+                            p->forcing_scheme, p->sgs_rho_power == 2 ? 2 : 1, fout, rho, u);
+}
+
 static double drag_factor(const olbm* s, int x, int y)
 {
     if (s->lad == NULL) return 0.0;
@@ -287,6 +370,10 @@ olbm* olbm_create(const olbm_params* p, const double* lad, const double* u_profi
 {
     if (p == NULL || p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
     if (p->tau0 <= 0.5 || p->stats_xbins < 1 || p->stats_xbins > p->nx) return NULL;
+    if (p->drag_streamwise_only < 0 || p->drag_streamwise_only > 1 ||
+        (p->forcing_scheme != OLBM_GUO && p->forcing_scheme != OLBM_EXACT_DIFFERENCE) ||
+        p->sgs_rho_power < 0 || p->sgs_rho_power > 2)
+        return NULL;
     int xper = p->bc_x_lo == OBC_PERIODIC && p->bc_x_hi == OBC_PERIODIC;
     int xio = p->bc_x_lo == OBC_INFLOW && p->bc_x_hi == OBC_OUTFLOW;
     int yper = p->bc_y_lo == OBC_PERIODIC && p->bc_y_hi == OBC_PERIODIC;
@@ -371,7 +458,7 @@ static void one_step(olbm* s)
                     gc[0] += a[0];
                     gc[2] += a[1];
                 }
-                olbm_collide_cell(fin, gc, drag_factor(s, x, y), p->tau0, p->cs, fout, &rho, u);
+                collide(s, fin, gc, drag_factor(s, x, y), fout, &rho, u);
                 size_t c = cell_index(s, x, y, z);
                 for (int i = 0; i < Q; i++) s->ftmp[(size_t)i * s->n + c] = fout[i];
                 s->cell_rho[c] = rho;
@@ -427,7 +514,7 @@ void olbm_macro(const olbm* s, double* rho_out, double* u_out)
             for (int x = 0; x < p->nx; x++) {
                 double fin[Q], fout[Q], rho, u[3];
                 for (int i = 0; i < Q; i++) fin[i] = pull_population(s, s->f, i, x, y, z);
-                olbm_collide_cell(fin, g, drag_factor(s, x, y), p->tau0, p->cs, fout, &rho, u);
+                collide(s, fin, g, drag_factor(s, x, y), fout, &rho, u);
                 size_t c = cell_index(s, x, y, z);
                 rho_out[c] = rho;
                 for (int a = 0; a < 3; a++) u_out[(size_t)a * s->n + c] = u[a];
@@ -453,9 +540,16 @@ void olbm_fields(const olbm* s, double* rho_out, double* u_out, double* strain_o
                 }
                 double v[3], u[3];
                 for (int a = 0; a < 3; a++) v[a] = (m[a] + 0.5 * rho * g[a]) / rho;
-                olbm_canopy_velocity(v, drag_factor(s, x, y), u);
+                double k = drag_factor(s, x, y);
+                if (p->drag_streamwise_only) olbm_canopy_velocity_x(v, k, u);
+                else olbm_canopy_velocity(v, k, u);
+                /* the equilibrium the collision relaxes towards: at u, or at
+                 * the bare velocity m / rho with exact-difference forcing */
+                double urel[3];
+                for (int a = 0; a < 3; a++)
+                    urel[a] = p->forcing_scheme == OLBM_EXACT_DIFFERENCE ? m[a] / rho : u[a];
                 double feq[Q];
-                olbm_feq(rho, u, feq);
+                olbm_feq(rho, urel, feq);
                 double pi[6] = {0, 0, 0, 0, 0, 0};
                 for (int i = 0; i < Q; i++) {
                     double d = fin[i] - feq[i];
@@ -468,7 +562,7 @@ void olbm_fields(const olbm* s, double* rho_out, double* u_out, double* strain_o
                 }
                 double q = sqrt(pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
                                 2.0 * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]));
-                double tau = olbm_tau_total(p->tau0, p->cs, rho, pi);
+                double tau = olbm_tau_total_p(p->tau0, p->cs, rho, pi, p->sgs_rho_power == 2 ? 2 : 1);
                 /* Pi_neq = -2 rho c_s^2 tau S (Chapman-Enskog, the relation
                  * behind Eq. strain), so |S| = sqrt(2 S:S) = sqrt(2) Q^1/2 / (2 rho c_s^2 tau) */
                 size_t c = cell_index(s, x, y, z);

@@ -54,7 +54,14 @@ typedef struct olbm_params {
     int32_t pad0;
     uint64_t seed;        /* seed of the initial velocity perturbation */
     double init_perturb;  /* amplitude of the uniform initial perturbation */
+    /* model variants (0 = default) */
+    int32_t drag_streamwise_only; /* 1: the canopy drag acts on u_x only */
+    int32_t forcing_scheme;       /* OLBM_GUO or OLBM_EXACT_DIFFERENCE */
+    int32_t sgs_rho_power;        /* 0/1: Q^1/2 / rho under the root of tau_total; 2: / rho^2 */
+    int32_t pad1;
 } olbm_params;
+
+enum { OLBM_GUO = 0, OLBM_EXACT_DIFFERENCE = 1 };
 
 typedef struct olbm olbm;
 
@@ -103,6 +110,21 @@ void olbm_canopy_velocity(const double v[3], double k, double u[3]);
 void olbm_collide_cell(const double fin[19], const double g_drive[3], double k,
                        double tau0, double cs, double fout[19],
                        double* rho_out, double u_out[3]);
+/* ---- model variants ---- */
+/* Streamwise-only drag: u_y = v_y, u_z = v_z and u_x the root of
+ * u_x (1 + (k/2) |u|) = v_x, |u|^2 = u_x^2 + v_y^2 + v_z^2 (by bisection). */
+void olbm_canopy_velocity_x(const double v[3], double k, double u[3]);
+/* tau_total with Q^1/2 / rho^p under the root, p = 1 or 2. */
+double olbm_tau_total_p(double tau0, double cs, double rho, const double pineq[6], int p);
+/* Exact-difference force term f_eq(rho, u + g) - f_eq(rho, u). */
+void olbm_edm_force(double rho, const double u[3], const double g[3], double Fi[19]);
+/* olbm_collide_cell with the variants: drag_x_only, scheme (OLBM_GUO or
+ * OLBM_EXACT_DIFFERENCE), rho_power (1 or 2).  u_out is the physical
+ * (force-corrected) velocity. */
+void olbm_collide_cell_model(const double fin[19], const double g_drive[3], double k,
+                             double tau0, double cs, int drag_x_only, int scheme,
+                             int rho_power, double fout[19], double* rho_out,
+                             double u_out[3]);
 /* Counter-based uniform draw in [-1, 1): n-th output of splitmix64 seeded
  * with seed, mapped through the top 53 bits. */
 double olbm_uniform(uint64_t seed, uint64_t n);

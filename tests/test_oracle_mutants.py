@@ -106,6 +106,35 @@ def _stats_error():
         return 1.0
 
 
+def _fails(fn, *args):
+    """1.0 if the pin `fn` fails (AssertionError) on the loaded oracle, else 0.0."""
+    try:
+        fn(*args)
+        return 0.0
+    except AssertionError:
+        return 1.0
+
+
+def _edm_moments_error():
+    from test_oracle_variants import test_exact_difference_force_moments as t
+    return _fails(t, 0)
+
+
+def _edm_recurrence_error():
+    from test_oracle_variants import test_exact_difference_momentum_recurrence_with_drag_and_driving as t
+    return _fails(t)
+
+
+def _streamwise_drag_error():
+    from test_oracle_variants import test_streamwise_drag_momentum_recurrence as t
+    return _fails(t, 0)
+
+
+def _tau_rho2_error():
+    from test_oracle_variants import test_tau_total_rho2_is_the_root_of_its_quadratic as t
+    return _fails(t, 0)
+
+
 MUTANTS = [
     ("guo_prefactor", "Fi[i] = (1.0 - 1.0 / (2.0 * tau))", "Fi[i] = (1.0 - 1.0 / tau)",
      _poiseuille_error, 1e-6),
@@ -127,6 +156,17 @@ MUTANTS = [
      _drag_error, 0.5),
     ("cov_sign", "out[6 * nb + k] = s->acc[6 * nb + k] / n - mu * mv;",
      "out[6 * nb + k] = s->acc[6 * nb + k] / n + mu * mv;", _stats_error, 0.5),
+    # model variants
+    ("edm_half_step", "double ug[3] = {u[0] + g[0], u[1] + g[1], u[2] + g[2]};",
+     "double ug[3] = {u[0] + 0.5 * g[0], u[1] + 0.5 * g[1], u[2] + 0.5 * g[2]};",
+     _edm_moments_error, 0.5),
+    ("edm_relaxes_to_physical_u",
+     "urel[a] = (scheme == OLBM_EXACT_DIFFERENCE) ? m[a] / rho : u[a];", "urel[a] = u[a];",
+     _edm_recurrence_error, 0.5),
+    ("streamwise_drag_on_all_components", "if (drag_x_only) g[0] -= k * un * u[0];",
+     "if (0) g[0] -= k * un * u[0];", _streamwise_drag_error, 0.5),
+    ("tau_rho_power_ignored", "double rp = (p == 2) ? rho * rho : rho;", "double rp = rho;",
+     _tau_rho2_error, 0.5),
 ]
 
 

@@ -46,6 +46,11 @@ class Case:
     init_perturb: float = 0.0
     lad: Optional[np.ndarray] = None
     u_profile: Optional[np.ndarray] = None
+    # model variants (0 = default): canopy drag on u_x only; forcing scheme
+    # (0 Guo, 1 exact difference); tau_total with Q^1/2 / rho^p, p = 1 (0) or 2
+    drag_streamwise_only: int = 0
+    forcing_scheme: int = 0
+    sgs_rho_power: int = 0
 
     @property
     def cells(self) -> int:
