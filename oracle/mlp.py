@@ -18,11 +18,12 @@ L = mean over samples and outputs of (o - (y - y_mean) / y_std)^2, with Adam
 the cells at y = 0: a = (lam * du_x - dtau_x, lam * du_z - dtau_z).
 
 Pins: the forward pass, the gradient, Adam and the BF16 rounding are pinned
-against closed forms, central differences and known values.  The correction
-rule itself (correction_accel: how the four outputs become an acceleration)
-has no definition outside this project, so it is "parity unpinned": it is
-only checked for self-consistency; its measure is the gain test against the
-coarsened finer run.
+against closed forms, central differences and known values; the correction
+rule (correction_accel: how the four outputs become an acceleration) is
+pinned on hand-set outputs, one output at a time, with a planted swap of the
+two stress outputs caught.  The rule has no definition outside this project
+(the paper has no learned part); whether it helps is measured by the gain
+test against the coarsened finer run.
 
 Parameters travel as one flat FP32/FP64 vector in this order:
 W1, b1, W2, b2, W3, b3, W4, b4 (row-major, rows = outputs), then

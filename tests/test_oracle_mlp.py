@@ -160,3 +160,52 @@ def test_layer0_acceleration_adds_exactly_rho_a_of_momentum():
     assert np.all(dm[:, 1:, :] == 0.0)           # other layers untouched in this step
     assert abs(o1.mass() - o2.mass()) < 1e-12 * o1.mass()
     o2.set_layer0_accel(None)
+
+
+def _bias_net(b4):
+    """A network whose last layer has zero weights: every row outputs its bias
+    b4 (y_mean = 0, y_std = 1)."""
+    layers = [(np.zeros((64, 9)), np.zeros(64)), (np.zeros((64, 64)), np.zeros(64)),
+              (np.zeros((64, 64)), np.zeros(64)), (np.zeros((4, 64)), np.asarray(b4, float))]
+    norm = (np.zeros(9), np.ones(9), np.zeros(4), np.ones(4))
+    return M.pack(layers, norm)
+
+
+def _check_correction_accel(mod):
+    """The outputs are (du_x, du_z, dtau_x, dtau_z): velocity deficits of the
+    first cell (fine minus coarse) and net retarding-stress deficits.  The
+    acceleration relaxes the velocity deficit at rate lam and adds the missing
+    retardation with a minus sign, per direction: for outputs (3, 5, 7, 11) and
+    lam = 0.5 that is (0.5*3 - 7, 0.5*5 - 11) = (-5.5, -8.5)."""
+    X = np.random.default_rng(3).normal(size=(5, 9))
+    a = mod.correction_accel(_bias_net([3.0, 5.0, 7.0, 11.0]), X, 0.5)
+    assert a.shape == (5, 2)
+    assert np.all(a[:, 0] == -5.5) and np.all(a[:, 1] == -8.5)
+    # meanings one output at a time: a faster fine run (du_x > 0) accelerates
+    # the coarse cell in x only; a larger fine-run stress deficit (dtau_z > 0)
+    # decelerates in z only
+    a = mod.correction_accel(_bias_net([2.0, 0.0, 0.0, 0.0]), X, 0.25)
+    assert np.all(a[:, 0] == 0.5) and np.all(a[:, 1] == 0.0)
+    a = mod.correction_accel(_bias_net([0.0, 0.0, 0.0, 4.0]), X, 0.25)
+    assert np.all(a[:, 0] == 0.0) and np.all(a[:, 1] == -4.0)
+
+
+def test_correction_accel_on_hand_set_outputs():
+    _check_correction_accel(M)
+
+
+def test_correction_accel_pin_catches_swapped_stress_outputs(tmp_path):
+    """Plant the mistake (dtau_x and dtau_z swapped) in a copy of the oracle's
+    network module, on the CPU: the pin above must fail."""
+    import importlib.util
+
+    src = open(M.__file__).read()
+    old = "lam * y[:, 0] - y[:, 2], lam * y[:, 1] - y[:, 3]"
+    assert src.count(old) == 1
+    path = tmp_path / "mlp_mutant.py"
+    path.write_text(src.replace(old, "lam * y[:, 0] - y[:, 3], lam * y[:, 1] - y[:, 2]"))
+    spec = importlib.util.spec_from_file_location("mlp_mutant", path)
+    mutant = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mutant)
+    with pytest.raises(AssertionError):
+        _check_correction_accel(mutant)
