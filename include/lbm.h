@@ -72,17 +72,27 @@ typedef enum lbm_status {
                              of the step fell outside its buffer and was skipped */
 } lbm_status;
 
-/* Boundary kinds.  Supported combinations: x periodic or INFLOW(x_lo) with
- * OUTFLOW(x_hi); y periodic, or BOUNCEBACK at y_lo with BOUNCEBACK,
- * FREESLIP or EQUILIBRIUM at y_hi; z periodic. */
+/* Boundary kinds.  Supported combinations: x periodic, INFLOW(x_lo) with
+ * OUTFLOW(x_hi), or HALO at both x faces; y periodic, or BOUNCEBACK at y_lo
+ * with BOUNCEBACK, FREESLIP or EQUILIBRIUM at y_hi; z periodic. */
 typedef enum lbm_bc {
     LBM_BC_PERIODIC = 0,
     LBM_BC_BOUNCEBACK = 1,  /* halfway bounce-back (no-slip wall half a cell out) */
     LBM_BC_FREESLIP = 2,    /* specular reflection of the wall-normal component */
     LBM_BC_EQUILIBRIUM = 3, /* incoming populations = f_eq(rho = 1, u_top) */
     LBM_BC_INFLOW = 4,      /* incoming populations = f_eq(rho = 1, u_in(y)) */
-    LBM_BC_OUTFLOW = 5      /* incoming populations copied from the last column */
+    LBM_BC_OUTFLOW = 5,     /* incoming populations copied from the last column */
+    LBM_BC_HALO = 6         /* x faces of one slab of a larger domain: incoming populations
+                               come from the neighbouring slabs through lbm_halo_pack /
+                               lbm_halo_unpack (both x faces) */
 } lbm_bc;
+
+/* Forcing scheme (lbm_forcing.scheme). */
+typedef enum lbm_force_scheme {
+    LBM_FORCE_GUO = 0,              /* Eq. bodyforce (Guo), velocity shifted by F/2 (Eq. momentum) */
+    LBM_FORCE_EXACT_DIFFERENCE = 1  /* Kupershtokh: relax towards f_eq(rho, u_b), u_b = m/rho,
+                                       and add f_eq(rho, u_b + g) - f_eq(rho, u_b) */
+} lbm_force_scheme;
 
 typedef enum lbm_storage {
     LBM_F32 = 0,        /* f_i - w_i in FP32: 152 bytes moved per lattice update */
@@ -108,6 +118,19 @@ typedef struct lbm_forcing {
     double u_top[3];        /* velocity of an EQUILIBRIUM top boundary */
     const double* u_in_profile; /* ny streamwise velocities, or NULL (= 0): the
                                    inflow profile and the initial mean profile */
+    /* Model variants (all 0 = the default model).  A context with any of them
+     * on runs the variant form of the step kernel; ensembles take the default
+     * model only. */
+    int32_t drag_streamwise_only; /* 1: the canopy drag acts on u_x alone,
+                                     g_c = (-C_D a |u| u_x, 0, 0) (Eq. forestForce read
+                                     as a streamwise force, as Sec. 2.3 describes it);
+                                     0: on the velocity vector, g_c = -C_D a |u| u */
+    int32_t scheme;               /* lbm_force_scheme */
+    int32_t sgs_rho_power;        /* 0 or 1: tau_total = (tau0 + sqrt(tau0^2 + 18 sqrt(2)
+                                     C_s^2 Q^1/2 / rho)) / 2 (Eq. strain solved for tau);
+                                     2: Q^1/2 / rho^2 under the root (the tau_total
+                                     equation as printed in Sec. 2.2) */
+    int32_t reserved;             /* must be 0 */
 } lbm_forcing;
 
 /* Bytes of device workspace lbm_create needs for this grid and storage;
@@ -209,6 +232,29 @@ lbm_status lbm_get_q(lbm_ctx* ctx, double* q, size_t n);
  * overlap on the GPU (other threads or streams) race.  Synchronises the
  * context's stream. */
 lbm_status lbm_get_macro_noalloc(lbm_ctx* ctx, double* rho, double* u, size_t n);
+
+/* ---- x-slab decomposition: halo exchange ----------------------------------------
+ * One domain cut along x into slabs, each an lbm_ctx whose x faces are
+ * LBM_BC_HALO (no bulk-velocity controller: it needs a global sum).  Per step
+ * a face passes on only what streams across it (Eq. lbe): the five
+ * populations with c_x = -1 of the slab's first column go to the left
+ * neighbour, the five with c_x = +1 of its last column to the right one.
+ * After every lbm_step (and once after lbm_create or lbm_set_f, before the
+ * first step) each slab calls lbm_halo_pack, the caller moves the faces
+ * (cudaMemcpyAsync, NCCL send/receive, ...), and each slab calls
+ * lbm_halo_unpack with what it received.
+ * Face buffers are caller-owned DEVICE memory of lbm_halo_bytes() bytes each,
+ * 16-byte aligned, layout [d][y][z] in the storage type (shifted like the
+ * populations), d indexing directions 1, 7, 9, 11, 13 (c_x = +1) or
+ * 2, 8, 10, 12, 14 (c_x = -1).  Both calls are asynchronous on the context's
+ * stream; LBM_ERR_ARG if the context has no halo faces or a pointer is NULL. */
+size_t lbm_halo_bytes(const lbm_ctx* ctx);
+/* to_lo <- c_x = -1 populations of column 0; to_hi <- c_x = +1 populations of
+ * column nx - 1 (the post-collision state of the last step). */
+lbm_status lbm_halo_pack(lbm_ctx* ctx, void* to_lo, void* to_hi);
+/* from_lo: the left neighbour's to_hi; from_hi: the right neighbour's to_lo.
+ * Written into the ghost slots the next step reads. */
+lbm_status lbm_halo_unpack(lbm_ctx* ctx, const void* from_lo, const void* from_hi);
 
 /* Driving acceleration the next step uses and the bulk velocity of the last. */
 lbm_status lbm_drive(lbm_ctx* ctx, double g[3], double* u_bulk);

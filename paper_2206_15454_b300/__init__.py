@@ -20,7 +20,8 @@ Q = 19
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NAN, LBM_ERR_TIMEOUT, \
     LBM_ERR_STATE, LBM_ERR_IO, LBM_ERR_BOUNDS = range(9)
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK, LBM_BC_FREESLIP, LBM_BC_EQUILIBRIUM, LBM_BC_INFLOW, \
-    LBM_BC_OUTFLOW = range(6)
+    LBM_BC_OUTFLOW, LBM_BC_HALO = range(7)
+LBM_FORCE_GUO, LBM_FORCE_EXACT_DIFFERENCE = range(2)
 LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = range(3)
 STORAGE_NAMES = {"f32": LBM_F32, "f16s": LBM_F16_SHIFTED, "bf16s": LBM_BF16_SHIFTED}
 BYTES_PER_LUP = {LBM_F32: 152, LBM_F16_SHIFTED: 76, LBM_BF16_SHIFTED: 76}
@@ -36,7 +37,9 @@ class LbmForcing(C.Structure):
     _fields_ = [("g", C.c_double * 3), ("cd", C.c_double),
                 ("x_canopy_begin", C.c_int32), ("x_canopy_end", C.c_int32),
                 ("u_bulk_target", C.c_double), ("ctrl_gain", C.c_double),
-                ("u_top", C.c_double * 3), ("u_in_profile", C.POINTER(C.c_double))]
+                ("u_top", C.c_double * 3), ("u_in_profile", C.POINTER(C.c_double)),
+                ("drag_streamwise_only", C.c_int32), ("scheme", C.c_int32),
+                ("sgs_rho_power", C.c_int32), ("reserved", C.c_int32)]
 
 
 class LbmBox(C.Structure):
@@ -79,6 +82,7 @@ def lib():
                            ("lbm_get_macro_noalloc", [vp, _DP, _DP, C.c_size_t]),
                            ("lbm_get_q", [vp, _DP, C.c_size_t]),
                            ("lbm_test_withhold_fill", [vp, C.c_int32]),
+                           ("lbm_halo_pack", [vp, vp, vp]), ("lbm_halo_unpack", [vp, vp, vp]),
                            ("lbm_drive", [vp, _DP, _DP]), ("lbm_save", [vp, C.c_char_p]),
                            ("lbm_load", [vp, C.c_char_p])]:
             fn = getattr(L, name)
@@ -125,6 +129,8 @@ def lib():
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_batch_last_error.restype = C.c_char_p
         L.lbm_batch_last_error.argtypes = [vp]
+        L.lbm_halo_bytes.restype = C.c_size_t
+        L.lbm_halo_bytes.argtypes = [vp]
         L.lbm_steps_done.restype = C.c_int64
         L.lbm_steps_done.argtypes = [vp]
         L.lbm_destroy.restype = None
@@ -228,6 +234,21 @@ def lbm_get_macro_noalloc(ctx, rho: np.ndarray, u: np.ndarray):
     """lbm_get_macro without device allocation (static field buffer, <= 262144 cells)."""
     _check(lib().lbm_get_macro_noalloc(ctx, _dp(rho), _dp(u), rho.size), ctx,
            "lbm_get_macro_noalloc")
+
+
+def lbm_halo_bytes(ctx) -> int:
+    return int(lib().lbm_halo_bytes(ctx))
+
+
+def lbm_halo_pack(ctx, to_lo: int, to_hi: int):
+    """Pack the slab's outgoing faces into two device buffers (pointers)."""
+    _check(lib().lbm_halo_pack(ctx, C.c_void_p(to_lo), C.c_void_p(to_hi)), ctx, "lbm_halo_pack")
+
+
+def lbm_halo_unpack(ctx, from_lo: int, from_hi: int):
+    """Write received faces (device buffers) into the slab's halo ghost slots."""
+    _check(lib().lbm_halo_unpack(ctx, C.c_void_p(from_lo), C.c_void_p(from_hi)), ctx,
+           "lbm_halo_unpack")
 
 
 def lbm_drive(ctx):
@@ -569,6 +590,9 @@ def _case_inputs(case):
     fo.u_bulk_target, fo.ctrl_gain = case.u_bulk_target, case.ctrl_gain
     fo.u_top[:] = [float(v) for v in case.u_top]
     fo.u_in_profile = _dp(uprof) if uprof is not None else _DP()
+    fo.drag_streamwise_only = getattr(case, "drag_streamwise_only", 0)
+    fo.scheme = getattr(case, "forcing_scheme", 0)
+    fo.sgs_rho_power = getattr(case, "sgs_rho_power", 0)
     lad = None if case.lad is None else np.ascontiguousarray(case.lad, dtype=np.float64)
     return g, fo, lad, (uprof, lad)
 

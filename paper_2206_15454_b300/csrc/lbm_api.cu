@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -18,9 +19,8 @@
 #include <vector>
 
 #include "../../include/lbm.h"
-#include "lbm_device.cuh"
 #include "lbm_diag.cuh"
-#include "lbm_mlp.cuh"
+#include "lbm_kernels.h"
 
 using namespace lbm;
 
@@ -84,7 +84,8 @@ bool grid_ok(const lbm_grid* g) {
   const long long cells = (long long)g->nx * g->ny * g->nz;
   if (cells >= (1ll << 31)) return false;
   const bool xper = g->x_lo == LBM_BC_PERIODIC && g->x_hi == LBM_BC_PERIODIC;
-  const bool xio = g->x_lo == LBM_BC_INFLOW && g->x_hi == LBM_BC_OUTFLOW;
+  const bool xio = (g->x_lo == LBM_BC_INFLOW && g->x_hi == LBM_BC_OUTFLOW) ||
+                   (g->x_lo == LBM_BC_HALO && g->x_hi == LBM_BC_HALO);
   const bool yper = g->y_lo == LBM_BC_PERIODIC && g->y_hi == LBM_BC_PERIODIC;
   const bool ywall = g->y_lo == LBM_BC_BOUNCEBACK &&
                      (g->y_hi == LBM_BC_BOUNCEBACK || g->y_hi == LBM_BC_FREESLIP ||
@@ -115,6 +116,7 @@ struct lbm_ctx {
   int64_t stats_samples = 0;
   float* macro_buf = nullptr;
   int sm_count = 0, blocks_per_sm = 0;
+  int device = 0;             // the device the context was created on
   int last_grid = 0;          // blocks of the previous step launch (partials to sum)
   int nstage = 0;             // tiles in flight per block
   int test_withhold = -1;     // lbm_test_withhold_fill: fill block 0 skips in the next step
@@ -230,7 +232,7 @@ StepParams make_params(const lbm_ctx* c) {
   std::memset(&p, 0, sizeof(p));
   const lbm_grid& g = c->grid;
   p.nx = g.nx; p.ny = g.ny; p.nz = g.nz; p.nxc = c->sh.nxc;
-  p.x_io = g.x_lo == LBM_BC_INFLOW;
+  p.x_io = g.x_lo == LBM_BC_INFLOW ? X_INOUT : g.x_lo == LBM_BC_HALO ? X_HALO : X_PERIODIC;
   p.y_walls = g.y_lo == LBM_BC_BOUNCEBACK;
   p.top = g.y_hi == LBM_BC_BOUNCEBACK ? 1 : g.y_hi == LBM_BC_FREESLIP ? 2 : 3;
   p.tau0 = (float)c->tau0;
@@ -277,7 +279,10 @@ StepParams make_params(const lbm_ctx* c) {
   p.t_in_inv = 1.0f / (float)p.t_in;
   p.t_mid_inv = 1.0f / (float)p.t_mid;
   p.t_fast = p.ntiles < (1ll << 23);
-  p.io_one = p.x_io && g.nx - (c->sh.nxc - 1) * c->sh.xt == 1;
+  p.io_one = p.x_io == X_INOUT && g.nx - (c->sh.nxc - 1) * c->sh.xt == 1;
+  p.drag_x_only = c->forcing.drag_streamwise_only;
+  p.edm = c->forcing.scheme == LBM_FORCE_EXACT_DIFFERENCE;
+  p.tau_rho2 = c->forcing.sgs_rho_power == 2;
   p.state = c->state();
   p.src = c->fbuf(c->cur);
   p.dst = c->fbuf(1 - c->cur);
@@ -297,26 +302,18 @@ void dispatch(const lbm_ctx* c, Fn&& fn) {
   else by_storage(std::integral_constant<int, 256>());
 }
 
+bool uses_variant(const lbm_forcing& f) {
+  return f.drag_streamwise_only != 0 || f.scheme == LBM_FORCE_EXACT_DIFFERENCE ||
+         f.sgs_rho_power == 2;
+}
 
 template <int XT, int S>
 void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
   // programmatic dependent launch: the blocks of this step may start while the
   // previous step's last blocks finish; the kernel waits (griddepcontrol.wait)
   // before it touches memory the previous step wrote or reads
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(step_grid(c));
-  cfg.blockDim = c->block;
-  cfg.dynamicSmemBytes = c->stage_smem;
-  cfg.stream = c->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (stats)
-    cudaLaunchKernelEx(&cfg, step_kernel<XT, S, true>, p);
-  else
-    cudaLaunchKernelEx(&cfg, step_kernel<XT, S, false>, p);
+  Kern<XT, S>::step(dim3(step_grid(c)), c->block, c->stage_smem, c->stream, p, stats,
+                    uses_variant(c->forcing), true);
 }
 
 // Shared-memory stages: as many tiles in flight as fit beside three blocks
@@ -328,22 +325,12 @@ void plan_stages(lbm_ctx* c) {
   const size_t stage = (size_t)c->block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
   c->nstage = (int)std::max<size_t>(2, std::min<size_t>(8, (62 * 1024) / stage));
   c->stage_smem = c->nstage * stage;
-  cudaFuncSetAttribute(step_kernel<XT, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->stage_smem);
-  cudaFuncSetAttribute(step_kernel<XT, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)c->stage_smem);
-  cudaFuncSetAttribute(batch_step_kernel<XT, S, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->stage_smem);
-  cudaFuncSetAttribute(batch_step_kernel<XT, S, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->stage_smem);
+  Kern<XT, S>::configure(c->stage_smem);
 }
 
 template <int XT, int S>
 int occupancy(dim3 block, size_t smem) {
-  int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, step_kernel<XT, S, false>, block.x * block.y, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<XT, S, true>, block.x * block.y, smem);
-  return std::max(1, std::min(a, b));
+  return Kern<XT, S>::occupancy(block, smem);
 }
 
 // Ghost slots of both population sets from their cells: the current set
@@ -352,8 +339,8 @@ int occupancy(dim3 block, size_t smem) {
 template <int XT, int S>
 void launch_ghosts(const lbm_ctx* c) {
   StepParams p = make_params(c);
-  ghost_kernel<XT, S><<<c->sm_count * 4, 256, 0, c->stream>>>(p, c->fbuf(c->cur));
-  ghost_kernel<XT, S><<<c->sm_count * 4, 256, 0, c->stream>>>(p, c->fbuf(1 - c->cur));
+  Kern<XT, S>::ghosts(c->sm_count * 4, c->stream, p, c->fbuf(c->cur));
+  Kern<XT, S>::ghosts(c->sm_count * 4, c->stream, p, c->fbuf(1 - c->cur));
 }
 
 template <int XT, int S>
@@ -364,21 +351,21 @@ void launch_init(const lbm_ctx* c) {
   ip.u_prof = c->uprof_dev();
   ip.seed = c->seed;
   ip.amp = c->init_perturb;
-  init_kernel<XT, S><<<c->sm_count * 8, 256, 0, c->stream>>>(ip);
+  Kern<XT, S>::init(c->sm_count * 8, c->stream, ip);
   launch_ghosts<XT, S>(c);
 }
 
 template <int XT, int S>
 void launch_mass(const lbm_ctx* c) {
-  mass_partial_kernel<XT, S><<<kMassBlocks, 256, 0, c->stream>>>(
-      c->fbuf(c->cur), c->grid.nx, (long long)c->grid.ny * c->grid.nz, c->sh.nxc, c->mass_buf());
+  Kern<XT, S>::mass(kMassBlocks, c->stream, c->fbuf(c->cur), c->grid.nx,
+                    (long long)c->grid.ny * c->grid.nz, c->sh.nxc, c->mass_buf());
   mass_final_kernel<<<1, 32, 0, c->stream>>>(c->mass_buf(), kMassBlocks, (double)c->cells,
                                               c->mass_buf() + kMassBlocks);
 }
 
 template <int XT, int S>
 void launch_macro(const lbm_ctx* c, const StepParams& p, float* out) {
-  macro_kernel<XT, S><<<c->sm_count * 8, 256, 0, c->stream>>>(p, out);
+  Kern<XT, S>::macro(c->sm_count * 8, c->stream, p, out);
 }
 
 // The correction's inputs over all first-cell columns into X, and with th
@@ -389,14 +376,14 @@ void launch_correction(const lbm_ctx* c, const float* th, float* X) {
   const int fblocks = (int)std::max<long long>(1, std::min<long long>((cols + 255) / 256,
                                                                       (long long)c->sm_count * 16));
   dispatch(c, [&](auto xt, auto s) {
-    features_kernel<decltype(xt)::value, decltype(s)::value><<<fblocks, 256, 0, c->stream>>>(p, X);
+    Kern<decltype(xt)::value, decltype(s)::value>::features(fblocks, c->stream, p, X);
   });
   if (th) {
     const long long tiles = (cols + 15) / 16;
     // few blocks, many rows each: every block stages the weights once
     const int mblocks = (int)std::max<long long>(1, std::min<long long>((tiles + 3) / 4,
                                                                         (long long)c->sm_count * 2));
-    mlp_accel_kernel<<<mblocks, 128, 0, c->stream>>>(th, X, cols, c->lam, c->accel());
+    mlp_launch_accel(mblocks, c->stream, th, X, cols, c->lam, c->accel());
   }
 }
 
@@ -470,6 +457,12 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
     return LBM_ERR_ARG;
   if (forcing->u_bulk_target > 0.0 && !(forcing->ctrl_gain >= 0.0)) return LBM_ERR_ARG;
   if (grid->x_lo == LBM_BC_INFLOW && !forcing->u_in_profile) return LBM_ERR_ARG;
+  // a slab of a larger domain: the controller would need the global bulk velocity
+  if (grid->x_lo == LBM_BC_HALO && forcing->u_bulk_target > 0.0) return LBM_ERR_ARG;
+  if ((forcing->drag_streamwise_only != 0 && forcing->drag_streamwise_only != 1) ||
+      (forcing->scheme != LBM_FORCE_GUO && forcing->scheme != LBM_FORCE_EXACT_DIFFERENCE) ||
+      forcing->sgs_rho_power < 0 || forcing->sgs_rho_power > 2 || forcing->reserved != 0)
+    return LBM_ERR_ARG;
   if (workspace && workspace_bytes < need) return LBM_ERR_OOM;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return LBM_ERR_ARG;
 
@@ -499,6 +492,7 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
   };
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return bail(LBM_ERR_CUDA);
+  c->device = dev;
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return bail(LBM_ERR_CUDA);
   if (workspace) {
@@ -839,6 +833,41 @@ lbm_status lbm_drive(lbm_ctx* c, double g[3], double* u_bulk) {
   return LBM_OK;
 }
 
+// ---- x-slab halo exchange -------------------------------------------------------------
+size_t lbm_halo_bytes(const lbm_ctx* c) {
+  if (!c || c->grid.x_lo != LBM_BC_HALO) return 0;
+  return (size_t)5 * c->grid.ny * c->grid.nz * elem_bytes(c->storage);
+}
+
+namespace {
+lbm_status halo_call(lbm_ctx* c, const void* lo, const void* hi, bool pack, const char* who) {
+  if (c->grid.x_lo != LBM_BC_HALO) return arg_error(c, std::string(who) + ": the context has no halo faces");
+  if (!lo || !hi) return arg_error(c, std::string(who) + ": NULL face buffer");
+  if ((reinterpret_cast<uintptr_t>(lo) | reinterpret_cast<uintptr_t>(hi)) % 16 != 0)
+    return arg_error(c, std::string(who) + ": face buffers must be 16-byte aligned");
+  const StepParams p = make_params(c);
+  const long long n = 10ll * c->grid.ny * c->grid.nz;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, c->sm_count * 4ll));
+  dispatch(c, [&](auto xt, auto s) {
+    using K = Kern<decltype(xt)::value, decltype(s)::value>;
+    if (pack) K::halo_pack(blocks, c->stream, p, c->fbuf(c->cur), const_cast<void*>(lo), const_cast<void*>(hi));
+    else K::halo_unpack(blocks, c->stream, p, c->fbuf(c->cur), lo, hi);
+  });
+  CK(c, cudaGetLastError());
+  return LBM_OK;
+}
+}  // namespace
+
+lbm_status lbm_halo_pack(lbm_ctx* c, void* to_lo, void* to_hi) {
+  READY(c);
+  return halo_call(c, to_lo, to_hi, true, "lbm_halo_pack");
+}
+
+lbm_status lbm_halo_unpack(lbm_ctx* c, const void* from_lo, const void* from_hi) {
+  READY(c);
+  return halo_call(c, from_lo, from_hi, false, "lbm_halo_unpack");
+}
+
 // ---- checkpoint ----------------------------------------------------------------------
 namespace {
 struct CkptHeader {
@@ -941,7 +970,9 @@ namespace {
 constexpr long long kNoAllocMaxCells = 262144;  // 64^3 cells; 8 MB of FP64 on every device
 __device__ __align__(256) double g_noalloc_fields[4 * kNoAllocMaxCells];
 constexpr int kMaxDevices = 64;
-double* g_noalloc_ptr[kMaxDevices] = {};  // device address of the array, per device
+// device address of the array, per device; threads that race on the first
+// call all store the same value
+std::atomic<double*> g_noalloc_ptr[kMaxDevices] = {};
 }  // namespace
 
 lbm_status lbm_get_macro_noalloc(lbm_ctx* c, double* rho, double* u, size_t n) {
@@ -952,19 +983,21 @@ lbm_status lbm_get_macro_noalloc(lbm_ctx* c, double* rho, double* u, size_t n) {
                         "its static field buffer; use lbm_get_macro");
   int dev = 0;
   CK(c, cudaGetDevice(&dev));
+  if (dev != c->device)
+    return arg_error(c, "lbm_get_macro_noalloc: make the context's device the current device");
   if (dev < 0 || dev >= kMaxDevices) return arg_error(c, "lbm_get_macro_noalloc: device id out of range");
-  if (!g_noalloc_ptr[dev]) {
+  double* buf = g_noalloc_ptr[dev].load();
+  if (!buf) {
     // first call on this device: look up the array's device address (the
     // symbol itself is only a host-side stand-in)
     void* ptr = nullptr;
     CK(c, cudaGetSymbolAddress(&ptr, g_noalloc_fields));
-    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+    buf = static_cast<double*>(ptr);
+    g_noalloc_ptr[dev].store(buf);
   }
-  double* buf = g_noalloc_ptr[dev];
   const StepParams p = make_params(c);
   dispatch(c, [&](auto xt, auto s) {
-    macro_kernel<decltype(xt)::value, decltype(s)::value, double>
-        <<<c->sm_count * 8, 256, 0, c->stream>>>(p, buf);
+    Kern<decltype(xt)::value, decltype(s)::value>::macro_d(c->sm_count * 8, c->stream, p, buf);
   });
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);
@@ -1046,6 +1079,8 @@ bool batch_args_ok(int32_t nbox, const lbm_box* boxes, int32_t storage, int32_t 
   for (int i = 0; i < nbox; i++) {
     if (lbm_workspace_bytes(&boxes[i].grid, storage, nbins) == 0) return false;
     if (boxes[i].forcing.u_bulk_target > 0.0) return false;
+    // the ensemble kernel runs the default model on whole boxes
+    if (uses_variant(boxes[i].forcing) || boxes[i].grid.x_lo == LBM_BC_HALO) return false;
   }
   return true;
 }
@@ -1175,13 +1210,8 @@ lbm_status batch_graph(lbm_batch* b, int n, bool stats, cudaGraphExec_t* exec) {
     for (int k = 0; k < n; k++) {
       const StepParams* P = g.params + (k & 1) * nb;
       dispatch(c0, [&](auto xt, auto s) {
-        constexpr int XT = decltype(xt)::value, S = decltype(s)::value;
-        if (stats)
-          batch_step_kernel<XT, S, true><<<(int)b->work.size(), c0->block, c0->stage_smem,
-                                           b->capture>>>(P, b->work_dev);
-        else
-          batch_step_kernel<XT, S, false><<<(int)b->work.size(), c0->block, c0->stage_smem,
-                                            b->capture>>>(P, b->work_dev);
+        Kern<decltype(xt)::value, decltype(s)::value>::batch_step(
+            (int)b->work.size(), c0->block, c0->stage_smem, b->capture, P, b->work_dev, stats);
       });
     }
     e = cudaStreamEndCapture(b->capture, &graph);
@@ -1456,9 +1486,9 @@ void mlp_pass(lbm_mlp* m, const float* X, const float* Y, const int* idx, int n,
   float* D4 = D3 + 64ll * n;
   const int blocks = (n + 127) / 128;
   const float scale = 2.0f / (4.0f * (float)n_total);
-  mlp_train_fwd<<<blocks, 128, 0, m->stream>>>(m->theta, X, Y, idx, n, scale, H0, H1, H2, H3, D4,
-                                               m->sse);
-  mlp_train_bwd<<<blocks, 128, 0, m->stream>>>(m->theta, n, H1, H2, H3, D4, D1, D2, D3);
+  mlp_launch_train_fwd(blocks, m->stream, m->theta, X, Y, idx, n, scale, H0, H1, H2, H3, D4,
+                       m->sse);
+  mlp_launch_train_bwd(blocks, m->stream, m->theta, n, H1, H2, H3, D4, D1, D2, D3);
   cudaMemsetAsync(m->grad, 0, sizeof(float) * MLP_NW, m->stream);
   const int rows_per_slice = 256;
   const int slices = (n + rows_per_slice - 1) / rows_per_slice;
@@ -1468,8 +1498,8 @@ void mlp_pass(lbm_mlp* m, const float* X, const float* Y, const int* idx, int n,
   const int offw[4] = {OFF_W1, OFF_W2, OFF_W3, OFF_W4}, offb[4] = {OFF_B1, OFF_B2, OFF_B3, OFF_B4};
   for (int l = 0; l < 4; l++) {
     dim3 grid(slices, (nouts[l] + 3) / 4);
-    mlp_train_wgrad<<<grid, 256, 0, m->stream>>>(Ds[l], nouts[l], Hs[l], nins[l], n,
-                                                 rows_per_slice, m->grad + offw[l], m->grad + offb[l]);
+    mlp_launch_train_wgrad(grid, m->stream, Ds[l], nouts[l], Hs[l], nins[l], n, rows_per_slice,
+                           m->grad + offw[l], m->grad + offb[l]);
   }
 }
 
@@ -1532,7 +1562,7 @@ lbm_status lbm_mlp_forward(lbm_mlp* m, const float* X, int64_t n, float* Y) {
   cudaMemcpyAsync(buf, X, sizeof(float) * MLP_IN * n, cudaMemcpyHostToDevice, m->stream);
   const long long tiles = (n + 15) / 16;
   const int blocks = (int)std::max<long long>(1, std::min<long long>((tiles + 3) / 4, 4096));
-  mlp_infer_kernel<<<blocks, 128, 0, m->stream>>>(m->theta, buf, n, dY);
+  mlp_launch_infer(blocks, m->stream, m->theta, buf, n, dY);
   cudaMemcpyAsync(Y, dY, sizeof(float) * MLP_OUT * n, cudaMemcpyDeviceToHost, m->stream);
   const cudaError_t e = cudaStreamSynchronize(m->stream);
   cudaFree(buf);
@@ -1633,8 +1663,8 @@ lbm_status lbm_mlp_train(lbm_mlp* m, const float* X, const float* Y, int64_t n, 
       m->adam_t++;
       const double c1 = 1.0 / (1.0 - std::pow(0.9, (double)m->adam_t));
       const double c2 = 1.0 / (1.0 - std::pow(0.999, (double)m->adam_t));
-      mlp_adam<<<(MLP_NW + 255) / 256, 256, 0, m->stream>>>(m->theta, m->grad, m->adam_m, m->adam_v,
-                                                          MLP_NW, lr, (float)c1, (float)c2);
+      mlp_launch_adam((MLP_NW + 255) / 256, m->stream, m->theta, m->grad, m->adam_m, m->adam_v,
+                      MLP_NW, lr, (float)c1, (float)c2);
     }
     float sse = 0.f;
     cudaMemcpyAsync(&sse, m->sse, sizeof(float), cudaMemcpyDeviceToHost, m->stream);

@@ -122,8 +122,8 @@ struct StepParams {
   const void* src;
   void* dst;
   int nx, ny, nz, nxc;      // nxc chunks of XT cells per row
-  int x_io;                 // 1: inflow at x = 0, outflow at x = nx-1; 0: periodic
-  int io_one;               // x_io with a last chunk of one cell
+  int x_io;                 // x boundary mode: X_PERIODIC, X_INOUT or X_HALO
+  int io_one;               // X_INOUT with a last chunk of one cell
   int y_walls;              // 1: bounce-back bottom + `top` kind; 0: periodic
   int top;                  // 1 bounce-back, 2 free-slip, 3 equilibrium
   float tau0, c18;          // c18 = 18 sqrt(2) C_s^2
@@ -162,7 +162,16 @@ struct StepParams {
   // learned first-layer correction: extra (x, z) acceleration of the cells at
   // y = 0, per column [z][x], or nullptr
   const float2* accel0;
+  // model variants (read only by the variant form of the step kernel and by
+  // the read-outs): canopy drag on the streamwise component only (Eq.
+  // forestForce as worded), exact-difference forcing instead of Guo's (Eq.
+  // bodyforce), Q^1/2 / rho^2 under the root of tau_total (the tau_total
+  // equation as printed) instead of / rho (Eq. strain solved for tau)
+  int drag_x_only, edm, tau_rho2;
 };
+
+// x boundary modes of StepParams::x_io
+enum : int { X_PERIODIC = 0, X_INOUT = 1, X_HALO = 2 };
 
 // element index of population q at cell (x, y, z)
 template <int XT, int S>
@@ -204,10 +213,13 @@ __device__ __forceinline__ int row_source(const StepParams& p, int i, int dy, in
 
 // Source column of a shifted direction: x - c_x with periodic wrap, the
 // inflow column (x = -1: returns -1), or the outflow copy (clamped).
+// At an x-halo face the column outside (-1 or nx) is returned: its values sit
+// in the ghost slots the halo exchange filled.
 __device__ __forceinline__ int source_x(const StepParams& p, int x, int dx) {
   int xs = x - dx;
-  if (xs < 0) xs = p.x_io ? -1 : p.nx - 1;
-  if (xs >= p.nx) xs = p.x_io ? p.nx - 1 : 0;
+  if (p.x_io == X_HALO) return xs;
+  if (xs < 0) xs = p.x_io == X_INOUT ? -1 : p.nx - 1;
+  if (xs >= p.nx) xs = p.x_io == X_INOUT ? p.nx - 1 : 0;
   return xs;
 }
 
@@ -216,8 +228,11 @@ struct Macro {
 };
 
 // Directions come in pairs (i, i+1) with c_{i+1} = -c_i (i odd).  Pair sums
-// and differences give the moments with half the additions.
-__device__ __forceinline__ Macro moments(const float* f, float gx, float gy, float gz, float k) {
+// and differences give the moments with half the additions.  VAR: the model
+// variants may be on (drag_x_only: the drag acts on u_x alone).
+template <bool VAR = false>
+__device__ __forceinline__ Macro moments(const float* f, float gx, float gy, float gz, float k,
+                                         int drag_x_only = 0) {
   Macro m;
   float sm[NQ], df[NQ];
 #pragma unroll
@@ -245,7 +260,24 @@ __device__ __forceinline__ Macro moments(const float* f, float gx, float gy, flo
   float vy = (my + 0.5f * rho * gy) * inv_rho;
   float vz = (mz + 0.5f * rho * gz) * inv_rho;
   float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
-  if (k > 0.f) {
+  if (VAR && drag_x_only && k > 0.f) {
+    // ... and a streamwise canopy drag g_c = (-k |u| u_x, 0, 0): u_y = v_y,
+    // u_z = v_z, and u_x solves u_x (1 + (k/2) |u|) = v_x with
+    // |u|^2 = u_x^2 + v_y^2 + v_z^2 (monotone in u_x).  Newton from the
+    // vector-drag root, which is within O((k|v|)^2) of it: two steps reach
+    // FP32 rounding for k|v| << 1.
+    const float s2 = vy * vy + vz * vz;
+    float ux = vx * (2.0f / (1.0f + sqrtf(1.0f + 2.0f * k * sqrtf(vx * vx + s2))));
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+      const float r = sqrtf(ux * ux + s2);
+      const float phi = ux + 0.5f * k * ux * r - vx;
+      const float dphi = 1.0f + 0.5f * k * (r + (r > 0.f ? ux * ux / r : 0.f));
+      ux -= phi / dphi;
+    }
+    vx = ux;
+    Fx -= rho * k * sqrtf(ux * ux + s2) * ux;
+  } else if (k > 0.f) {
     // ... and the canopy part g_c = -k |u| u: u = v + g_c/2 gives u parallel
     // to v with |u| the positive root of (k/2) s^2 + s = |v|.
     const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
@@ -268,10 +300,20 @@ __device__ __forceinline__ Macro moments(const float* f, float gx, float gy, flo
 //   F_i      = (1 - om/2) W (9 e h - 3 u.F)      +- 3 (1 - om/2) W h (Eq. bodyforce)
 // so the even and odd parts are evaluated once per pair.  Pi_neq (Eq. tensor)
 // needs only the pair sums of f - f_eq.  The post-collision values
-// f* = f - om (f - f_eq) + F_i are handed to `emit(i, value)`.
+// f* = f - om (f - f_eq) + F_i are handed to `emit(i, value)`.  VAR: the
+// variants may be on (tau_rho2: Q^1/2 / rho^2 under the root of tau_total;
+// edm: the exact-difference forcing of collide_edm).
 template <class Emit>
+__device__ __forceinline__ void collide_edm(const float* f, const Macro& m, float tau0, float c18,
+                                            int tau_rho2, Emit&& emit);
+
+template <bool VAR = false, class Emit>
 __device__ __forceinline__ void collide(const float* f, const Macro& m, float tau0, float c18,
-                                        Emit&& emit) {
+                                        int edm, int tau_rho2, Emit&& emit) {
+  if (VAR && edm) {
+    collide_edm(f, m, tau0, c18, tau_rho2, emit);
+    return;
+  }
   const float ux = m.ux, uy = m.uy, uz = m.uz;
   const float uu = ux * ux + uy * uy + uz * uz;
   const float base = m.drho - 1.5f * m.rho * uu;  // even part without the e^2 term
@@ -300,7 +342,8 @@ __device__ __forceinline__ void collide(const float* f, const Macro& m, float ta
     if (cy(i) * cz(i) == -1) pyz -= npair;
   }
   const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
-  const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * sqrtf(q2) / m.rho));
+  const float rr = (VAR && tau_rho2) ? m.rho * m.rho : m.rho;
+  const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * sqrtf(q2) / rr));
   const float om = 1.0f / tau;
   const float keep = 1.0f - om;
   const float pre = 1.0f - 0.5f * om;
@@ -326,6 +369,56 @@ __device__ __forceinline__ void collide(const float* f, const Macro& m, float ta
     const float pw = pre * w;
     const float even = om * sym[i] + pw * (9.0f * ei * hi - uF3);
     const float odd = om * (w * r3 * ei) + 3.0f * pw * hi;
+    emit(i, keep * f[i] + (even + odd));
+    emit(i + 1, keep * f[i + 1] + (even - odd));
+  }
+}
+
+// Exact-difference forcing (Kupershtokh): relaxation towards f_eq(rho, u_b)
+// at the bare velocity u_b = m/rho = u - g/2 (u the force-corrected velocity
+// of `m`, g = F/rho the total acceleration), and the force term
+// F_i = f_eq(rho, u_b + g) - f_eq(rho, u_b).  With e = c_i . u_b, h = c_i . g:
+//   F_i = W rho (4.5 h (2e + h) - 3 u_b.g - 1.5 g.g) +- 3 W rho h,
+// even and odd parts per pair as in collide().  Pi_neq and tau_total use the
+// same f_eq(rho, u_b).
+template <class Emit>
+__device__ __forceinline__ void collide_edm(const float* f, const Macro& m, float tau0, float c18,
+                                            int tau_rho2, Emit&& emit) {
+  const float inv_rho = 1.0f / m.rho;
+  const float gx = m.Fx * inv_rho, gy = m.Fy * inv_rho, gz = m.Fz * inv_rho;
+  const float ux = m.ux - 0.5f * gx, uy = m.uy - 0.5f * gy, uz = m.uz - 0.5f * gz;
+  const float uu = ux * ux + uy * uy + uz * uz;
+  const float base = m.drho - 1.5f * m.rho * uu;
+  const float r45 = 4.5f * m.rho;
+  const float r3 = 3.0f * m.rho;
+  float sym[NQ];
+  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    const float ei = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    sym[i] = wgt(i) * (base + r45 * ei * ei);
+    const float npair = (f[i] + f[i + 1]) - 2.0f * sym[i];
+    if (cx(i) != 0) pxx += npair;
+    if (cy(i) != 0) pyy += npair;
+    if (cz(i) != 0) pzz += npair;
+    pxy += (float)(cx(i) * cy(i)) * npair;
+    pxz += (float)(cx(i) * cz(i)) * npair;
+    pyz += (float)(cy(i) * cz(i)) * npair;
+  }
+  const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
+  const float rr = tau_rho2 ? m.rho * m.rho : m.rho;
+  const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * sqrtf(q2) / rr));
+  const float om = 1.0f / tau;
+  const float keep = 1.0f - om;
+  const float ug = 3.0f * (ux * gx + uy * gy + uz * gz) + 1.5f * (gx * gx + gy * gy + gz * gz);
+  emit(0, keep * f[0] + om * (wgt(0) * base) - wgt(0) * m.rho * ug);
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    const float w = wgt(i);
+    const float ei = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const float hi = cx(i) * gx + cy(i) * gy + cz(i) * gz;
+    const float even = om * sym[i] + w * m.rho * (4.5f * hi * (2.0f * ei + hi) - ug);
+    const float odd = om * (w * r3 * ei) + w * r3 * hi;
     emit(i, keep * f[i] + (even + odd));
     emit(i + 1, keep * f[i + 1] + (even - odd));
   }
@@ -594,7 +687,7 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
 // a tile and the consumers may leave at the first empty stage with no copy in
 // flight.  (Issuing prologue fills from several warps at once broke this and
 // let a block end with copies still landing in its shared memory.)
-template <int XT, int S, bool STATS>
+template <int XT, int S, bool STATS, bool VAR>
 __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part,
                                            bool dynamic) {
   using T = typename Store<S>::T;
@@ -783,9 +876,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       }
       if (p.accel0 != nullptr && y == 0) {
         const float2 a = p.accel0[(long long)z * p.nx + x];
-        m = moments(f, gx + a.x, gy, gz + a.y, drag_factor(p, x, y));
+        m = moments<VAR>(f, gx + a.x, gy, gz + a.y, drag_factor(p, x, y), p.drag_x_only);
       } else {
-        m = moments(f, gx, gy, gz, drag_factor(p, x, y));
+        m = moments<VAR>(f, gx, gy, gz, drag_factor(p, x, y), p.drag_x_only);
       }
     }
     // release the stage: the moments consumed every staged value of this warp
@@ -797,18 +890,19 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       // ghost slots this cell feeds (edge lanes only): its c_x = +1 values to
       // the left ghost of the chunk on its right, its c_x = -1 values to the
       // right ghost of the chunk on its left (periodic wrap), or beside itself
-      // at an outflow (zero gradient)
+      // at an outflow (zero gradient); at an x-halo face none (the halo
+      // exchange sends them to the neighbouring slab and fills these ghosts)
       T* gr = nullptr;
       T* gl = nullptr;
       if (tx == 0 || tx == XT - 1 || x == p.nx - 1) {
         if (x == p.nx - 1) {
-          if (!p.x_io) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
-          else gl = out + 1;  // outflow: its own slot G + n (a one-cell last chunk: below)
+          if (p.x_io == X_PERIODIC) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
+          else if (p.x_io == X_INOUT) gl = out + 1;  // outflow: its own slot G + n (a one-cell last chunk: below)
         } else if (tx == XT - 1) {
           gr = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
         }
         if (x == 0) {
-          if (!p.x_io) {
+          if (p.x_io == X_PERIODIC) {
             const int xl = p.nxc - 1;
             gl = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
           }
@@ -816,7 +910,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           gl = dst0 + (long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT;
         }
       }
-      collide(f, m, p.tau0, p.c18, [&](int i, float v) {
+      collide<VAR>(f, m, p.tau0, p.c18, p.edm, p.tau_rho2, [&](int i, float v) {
         if (kCheckBounds) {
           const long long set = (long long)p.ny * p.nz * p.nxc * Gm::ROW;
           T* const d0 = static_cast<T*>(p.dst);
@@ -859,21 +953,27 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   // Leave no copy in flight when the block ends: after a timed-out wait some
   // issued fills were never consumed.  (On the normal path every issued fill
   // has completed; the waits return at once.)  finish_step ended with a
-  // block barrier, so s_nfill is final.
+  // block barrier, so s_nfill is final.  A drain wait that runs out too (a
+  // copy still landing after about a second) is reported as a timeout: the
+  // block then ends with that copy in flight and the context is unusable.
   if (tid == 0) {
     const int nf = s_nfill;
+    bool drained = true;
     for (int k = 0; k < p.nstage && k < nf; k++) {
       const int uses = (nf - 1 - k) / p.nstage + 1;  // fills that went into stage k
-      mbar_wait(&s_bar[k], (uint32_t)((uses - 1) & 1), WAIT_LIMIT);
+      drained &= mbar_wait(&s_bar[k], (uint32_t)((uses - 1) & 1), WAIT_LIMIT);
     }
+    if (!drained) atomicOr(&p.state->timeout_flag, 1u);
   }
 }
 
 // One domain: block b walks its static run of tiles, then shares the rest.
-template <int XT, int S, bool STATS>
+// VAR: the model-variant form (flags in p); the default form has none of
+// their code.
+template <int XT, int S, bool STATS, bool VAR>
 __global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
-  step_tiles<XT, S, STATS>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles, blockIdx.x,
-                           true);
+  step_tiles<XT, S, STATS, VAR>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
+                                blockIdx.x, true);
 }
 
 // Many independent domains (an ensemble of boxes) in one launch: work item
@@ -898,12 +998,13 @@ __global__ void __launch_bounds__(256, 3) batch_step_kernel(const StepParams* __
       dst[k] = src[k];
   }
   __syncthreads();
-  step_tiles<XT, S, STATS>(s_p, w.t0, w.ntile, -1, false);
+  step_tiles<XT, S, STATS, false>(s_p, w.t0, w.ntile, -1, false);
 }
 
 // ---- ghost slots from the cells (after init, set_f) ----------------------------------
 // One thread per (chunk-row, side, direction with c_x != 0).  The inflow
-// ghosts hold the inflow equilibrium and are never rewritten by a step.
+// ghosts hold the inflow equilibrium and are never rewritten by a step; the
+// ghosts at an x-halo face are left to the halo exchange.
 template <int XT, int S>
 __global__ void ghost_kernel(StepParams p, void* fv) {
   using T = typename Store<S>::T;
@@ -924,13 +1025,63 @@ __global__ void ghost_kernel(StepParams p, void* fv) {
     auto cell = [&](int xc2, int t) { return f[((yz * p.nxc) + xc2) * Gm::ROW + (long long)i * Gm::XTP + t]; };
     if (j < 5) {
       if (xc > 0) row[-1] = cell(xc - 1, XT - 1);
-      else if (p.x_io) row[-1] = Store<S>::from_double((double)p.feq_in[y * NQ + i]);
-      else row[-1] = cell(p.nxc - 1, p.nx - 1 - (p.nxc - 1) * XT);
+      else if (p.x_io == X_INOUT) row[-1] = Store<S>::from_double((double)p.feq_in[y * NQ + i]);
+      else if (p.x_io == X_PERIODIC) row[-1] = cell(p.nxc - 1, p.nx - 1 - (p.nxc - 1) * XT);
     } else {
       if (xc < p.nxc - 1) row[n] = cell(xc + 1, 0);
-      else if (p.x_io) row[n] = row[n - 1];
-      else row[n] = cell(0, 0);
+      else if (p.x_io == X_INOUT) row[n] = row[n - 1];
+      else if (p.x_io == X_PERIODIC) row[n] = cell(0, 0);
     }
+  }
+}
+
+// ---- x-halo exchange of a slab (one domain cut into x-slabs) --------------------------
+// Per step a slab face passes on only what streams across it (Eq. lbe: the
+// pull reaches one column, and only for the five directions with c_x = +-1).
+// Face buffers are [d][y][z] in the storage type, d indexing the directions
+// 1, 7, 9, 11, 13 (c_x = +1) or 2, 8, 10, 12, 14 (c_x = -1).
+__host__ __device__ constexpr int halo_dir(int side, int d) {  // side 1: c_x = +1
+  return side ? (d == 0 ? 1 : 5 + 2 * d) : (d == 0 ? 2 : 6 + 2 * d);
+}
+
+// Pack the post-collision state f: lo <- the c_x = -1 values of column 0 (for
+// the left neighbour's right halo), hi <- the c_x = +1 values of column nx - 1
+// (for the right neighbour's left halo).
+template <int XT, int S>
+__global__ void halo_pack_kernel(StepParams p, const void* fv, void* lo, void* hi) {
+  using T = typename Store<S>::T;
+  const T* f = static_cast<const T*>(fv);
+  const long long per = (long long)p.ny * p.nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 10 * per;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int side = k >= 5 * per ? 1 : 0;
+    const long long r = k - side * 5 * per;
+    const int d = (int)(r / per);
+    const long long yz = r - d * per;
+    const int y = (int)(yz / p.nz), z = (int)(yz - (long long)y * p.nz);
+    const T v = f[pop_index<XT, S>(p, halo_dir(side, d), side ? p.nx - 1 : 0, y, z)];
+    static_cast<T*>(side ? hi : lo)[r] = v;
+  }
+}
+
+// Unpack received faces into the ghost slots of f (the state the next step
+// reads): lo (the left neighbour's c_x = +1 values) into slot G - 1 of chunk 0,
+// hi (the right neighbour's c_x = -1 values) into slot G + n of the last chunk.
+template <int XT, int S>
+__global__ void halo_unpack_kernel(StepParams p, void* fv, const void* lo, const void* hi) {
+  using T = typename Store<S>::T;
+  T* f = static_cast<T*>(fv);
+  const long long per = (long long)p.ny * p.nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 10 * per;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int side = k >= 5 * per ? 1 : 0;  // 0: from the left, 1: from the right
+    const long long r = k - side * 5 * per;
+    const int d = (int)(r / per);
+    const long long yz = r - d * per;
+    const int y = (int)(yz / p.nz), z = (int)(yz - (long long)y * p.nz);
+    const long long at = side ? pop_index<XT, S>(p, halo_dir(0, d), p.nx - 1, y, z) + 1
+                              : pop_index<XT, S>(p, halo_dir(1, d), 0, y, z) - 1;
+    f[at] = static_cast<const T*>(side ? hi : lo)[r];
   }
 }
 
@@ -1006,13 +1157,6 @@ __global__ void mass_partial_kernel(const void* fv, int nx, long long rows, int 
   if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
 }
 
-__global__ void mass_final_kernel(const double* partial, int n, double base, double* out) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < n; k++) s += partial[k];
-    *out = base + s;
-  }
-}
 
 // ---- macroscopic fields of the next step (pull + moments only) ------------------------
 // Direct loads with the same boundary rules as the step (not performance critical).
@@ -1032,16 +1176,24 @@ __device__ __forceinline__ void gather_cell(const StepParams& p, int x, int y, i
       f[i] = Store<S>::ld(src + pop_index<XT, S>(p, q, x, ys, zs));
     } else {
       const int xs = source_x(p, x, cx(i));
-      f[i] = xs < 0 ? p.feq_in[ys * NQ + q] : Store<S>::ld(src + pop_index<XT, S>(p, q, xs, ys, zs));
+      if (p.x_io == X_HALO && xs < 0)  // the left halo: ghost slot G - 1 of chunk 0
+        f[i] = Store<S>::ld(src + pop_index<XT, S>(p, q, 0, ys, zs) - 1);
+      else if (p.x_io == X_HALO && xs >= p.nx)  // the right halo: slot G + n of the last chunk
+        f[i] = Store<S>::ld(src + pop_index<XT, S>(p, q, p.nx - 1, ys, zs) + 1);
+      else
+        f[i] = xs < 0 ? p.feq_in[ys * NQ + q] : Store<S>::ld(src + pop_index<XT, S>(p, q, xs, ys, zs));
     }
   }
 }
 
 // Strain-rate magnitude |S| = sqrt(2 S:S) of a cell from its non-equilibrium
 // momentum flux (Eq. tensor) through Pi_neq = -2 rho c_s^2 tau_total S, with
-// tau_total from the Smagorinsky closure as in the collision.
-__device__ __forceinline__ float strain_rate(const float* f, const Macro& m, float tau0, float c18) {
-  const float ux = m.ux, uy = m.uy, uz = m.uz;
+// f_eq and tau_total as in the collision (the model variants included).
+__device__ __forceinline__ float strain_rate(const float* f, const Macro& m, float tau0, float c18,
+                                             int edm = 0, int tau_rho2 = 0) {
+  const float hx = edm ? 0.5f * m.Fx / m.rho : 0.f, hy = edm ? 0.5f * m.Fy / m.rho : 0.f,
+              hz = edm ? 0.5f * m.Fz / m.rho : 0.f;  // exact difference: f_eq at u - g/2
+  const float ux = m.ux - hx, uy = m.uy - hy, uz = m.uz - hz;
   const float base = m.drho - 1.5f * m.rho * (ux * ux + uy * uy + uz * uz);
   const float r45 = 4.5f * m.rho;
   float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
@@ -1058,7 +1210,7 @@ __device__ __forceinline__ float strain_rate(const float* f, const Macro& m, flo
   }
   const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
   const float q = sqrtf(q2);
-  const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * q / m.rho));
+  const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * q / (tau_rho2 ? m.rho * m.rho : m.rho)));
   return 2.1213203435596424f * q / (m.rho * tau);  // sqrt(2) / (2 c_s^2) = 3 / sqrt(2)
 }
 
@@ -1074,7 +1226,7 @@ __global__ void macro_kernel(StepParams p, OutT* out) {
     const int z = (int)(r / p.ny);
     float f[NQ];
     gather_cell<XT, S>(p, x, y, z, f);
-    const Macro m = moments(f, gx, p.g[1], p.g[2], drag_factor(p, x, y));
+    const Macro m = moments<true>(f, gx, p.g[1], p.g[2], drag_factor(p, x, y), p.drag_x_only);
     out[c] = m.rho;
     out[n + c] = m.ux;
     out[2 * n + c] = m.uy;

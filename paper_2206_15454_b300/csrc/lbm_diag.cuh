@@ -57,4 +57,14 @@ __global__ void q_kernel(const float* __restrict__ u, float* __restrict__ q, int
   }
 }
 
+// Second pass of the global mass (lbm_mass): the per-block partial sums in a
+// fixed order, plus the lattice-weight part of every cell (base = cells).
+__global__ void mass_final_kernel(const double* partial, int n, double base, double* out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s += partial[k];
+    *out = base + s;
+  }
+}
+
 }  // namespace lbm

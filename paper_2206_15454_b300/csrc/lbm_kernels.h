@@ -1,0 +1,70 @@
+// lbm_kernels.h -- host-side launchers of the per-(chunk width, storage)
+// kernels of lbm_device.cuh and lbm_mlp.cuh.
+//
+// Every kernel template is instantiated in one of three translation units
+// (lbm_kern_f32.cu, lbm_kern_f16.cu, lbm_kern_bf16.cu, one per storage type)
+// so the library compiles in parallel; the host code in lbm_api.cu only calls
+// these launchers.  All launches are asynchronous on the given stream; launch
+// errors surface through cudaGetLastError.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_features.cuh"
+
+namespace lbm {
+
+template <int XT, int S>
+struct Kern {
+  // Largest dynamic shared memory every step kernel may use (stage ring).
+  static void configure(size_t stage_smem);
+  // Resident blocks per SM of the step kernels (the smaller over their forms).
+  static int occupancy(dim3 block, size_t smem);
+  // One time step (programmatic dependent launch when pdl).  variant: the
+  // model-variant form (streamwise-only drag, exact-difference forcing,
+  // tau_total with 1/rho^2), selected by the flags in p.
+  static void step(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const StepParams& p,
+                   bool stats, bool variant, bool pdl);
+  // One time step of every box of an ensemble (work list w).
+  static void batch_step(int nblocks, dim3 block, size_t smem, cudaStream_t s,
+                         const StepParams* boxes, const BatchWork* w, bool stats);
+  static void ghosts(int blocks, cudaStream_t s, const StepParams& p, void* f);
+  static void init(int blocks, cudaStream_t s, const InitParams& ip);
+  static void mass(int blocks, cudaStream_t s, const void* f, int nx, long long rows, int nxc,
+                   double* partial);
+  static void macro(int blocks, cudaStream_t s, const StepParams& p, float* out);
+  static void macro_d(int blocks, cudaStream_t s, const StepParams& p, double* out);
+  static void features(int blocks, cudaStream_t s, const StepParams& p, float* X);
+  // x-halo faces of a slab: pack from / unpack into population set f.
+  static void halo_pack(int blocks, cudaStream_t s, const StepParams& p, const void* f, void* lo,
+                        void* hi);
+  static void halo_unpack(int blocks, cudaStream_t s, const StepParams& p, void* f, const void* lo,
+                          const void* hi);
+};
+
+// ---- the learned correction's network (lbm_mlp.cu; kernels in lbm_mlp.cuh) ----
+void mlp_launch_accel(int blocks, cudaStream_t s, const float* th, const float* X, long long n,
+                      float lam, float2* accel);
+void mlp_launch_infer(int blocks, cudaStream_t s, const float* th, const float* X, long long n,
+                      float* Y);
+void mlp_launch_train_fwd(int blocks, cudaStream_t s, const float* th, const float* X,
+                          const float* Y, const int* idx, int n, float scale, float* H0, float* H1,
+                          float* H2, float* H3, float* D4, float* sse);
+void mlp_launch_train_bwd(int blocks, cudaStream_t s, const float* th, int n, const float* H1,
+                          const float* H2, const float* H3, const float* D4, float* D1, float* D2,
+                          float* D3);
+void mlp_launch_train_wgrad(dim3 grid, cudaStream_t s, const float* D, int nout, const float* Hin,
+                            int nin, int n, int rows_per_slice, float* gW, float* gb);
+void mlp_launch_adam(int blocks, cudaStream_t s, float* th, const float* g, float* m, float* v,
+                     int n, float lr, float c1, float c2);
+
+#define LBM_DECLARE_KERN(SV)           \
+  extern template struct Kern<64, SV>; \
+  extern template struct Kern<128, SV>; \
+  extern template struct Kern<256, SV>;
+LBM_DECLARE_KERN(0)
+LBM_DECLARE_KERN(1)
+LBM_DECLARE_KERN(2)
+#undef LBM_DECLARE_KERN
+
+}  // namespace lbm

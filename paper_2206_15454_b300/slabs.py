@@ -113,3 +113,95 @@ def allreduce_sum(a: np.ndarray) -> np.ndarray:
     t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).clone()
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return t.numpy()
+
+
+# ---- the library's x-slab data path ------------------------------------------------
+
+def slab_case_halo(case, x0: int, x1: int):
+    """The slab [x0, x1) of a periodic-in-x case as a library domain whose x
+    faces are halos (LBM_BC_HALO): x1 - x0 columns, the neighbours' columns
+    living in the ghost slots that lbm_halo_unpack fills.  The canopy's
+    x-range moves with the slab; statistics are kept per plane."""
+    from . import LBM_BC_HALO
+
+    if tuple(case.bc_x) != (0, 0):
+        raise ValueError("the x-slab decomposition needs a periodic x direction")
+    if case.u_bulk_target > 0:
+        raise ValueError("a bulk-velocity controller needs a global sum every step")
+    c0, c1 = case.canopy_x
+    lo, hi = max(c0, x0), min(c1, x1)
+    canopy = (lo - x0, hi - x0) if lo < hi else (0, 0)
+    return case.replace(name=f"{case.name}_halo{x0}_{x1}", nx=x1 - x0, canopy_x=canopy,
+                        bc_x=(LBM_BC_HALO, LBM_BC_HALO), stats_xbins=1)
+
+
+class DeviceSlabs:
+    """One periodic-in-x domain cut into `nslabs` x-slabs, each an lbm_ctx with
+    halo faces, all on this GPU and stream.  Per step every slab steps, packs
+    its two outgoing faces into device buffers, the buffers are copied
+    device-to-device to the neighbours' receive buffers (the exchange a
+    multi-GPU run does with NCCL send/receive or peer copies into local
+    memory), and every slab unpacks what it received.  The state is set from a
+    global population array (public layout) and read back as one."""
+
+    def __init__(self, case, nslabs, storage=0):
+        import torch
+
+        from . import Domain, lbm_halo_bytes
+
+        self.case, self.storage = case, storage
+        self.bounds = [slab_bounds(case.nx, nslabs, r) for r in range(nslabs)]
+        self.doms = [Domain(slab_case_halo(case, x0, x1), storage) for x0, x1 in self.bounds]
+        nb = lbm_halo_bytes(self.doms[0].ctx)
+        mk = lambda: torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.send = [(mk(), mk()) for _ in self.doms]   # (to the left, to the right)
+        self.recv = [(mk(), mk()) for _ in self.doms]   # (from the left, from the right)
+
+    def exchange(self):
+        from . import lbm_halo_pack, lbm_halo_unpack
+
+        n = len(self.doms)
+        for d, (lo, hi) in zip(self.doms, self.send):
+            lbm_halo_pack(d.ctx, lo.data_ptr(), hi.data_ptr())
+        for r in range(n):
+            self.recv[r][0].copy_(self.send[(r - 1) % n][1])  # left neighbour's last column
+            self.recv[r][1].copy_(self.send[(r + 1) % n][0])  # right neighbour's first column
+        for d, (lo, hi) in zip(self.doms, self.recv):
+            lbm_halo_unpack(d.ctx, lo.data_ptr(), hi.data_ptr())
+
+    def set_f(self, f_global):
+        for d, (x0, x1) in zip(self.doms, self.bounds):
+            d.set_f(np.ascontiguousarray(f_global[..., x0:x1]))
+        self.exchange()
+
+    def step(self, n=1):
+        for _ in range(n):
+            for d in self.doms:
+                d.step(1)
+            self.exchange()
+
+    def get_f(self):
+        return np.concatenate([d.get_f() for d in self.doms], axis=-1)
+
+    def stats_reset(self, enable=True):
+        for d in self.doms:
+            d.stats_reset(enable)
+
+    def stats(self):
+        """Plane statistics of the whole domain from the slabs' (the plane sums
+        add up; the covariances are recombined from the slabs' raw moments)."""
+        out = [d.stats() for d in self.doms]
+        n = out[0][1]
+        w = np.array([x1 - x0 for x0, x1 in self.bounds], dtype=np.float64) / self.case.nx
+        mean = sum(wi * s[:3] for wi, (s, _) in zip(w, out))
+        pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        res = np.zeros_like(out[0][0])
+        res[:3] = mean
+        for k, (a, b) in enumerate(pairs):
+            raw = sum(wi * (s[3 + k] + s[a] * s[b]) for wi, (s, _) in zip(w, out))
+            res[3 + k] = raw - mean[a] * mean[b]
+        return res, n
+
+    def close(self):
+        for d in self.doms:
+            d.close()

@@ -92,6 +92,42 @@ def test_create_rejects_bad_arguments_without_a_device():
                         None) == P.LBM_ERR_ARG
 
 
+def test_model_variants_and_halo_checked_without_a_device():
+    L = P.lib()
+    ctx = C.c_void_p()
+    g = _grid()
+    for field, bad in (("drag_streamwise_only", 2), ("scheme", 2), ("sgs_rho_power", 3),
+                       ("reserved", 1)):
+        fo = P.LbmForcing()
+        setattr(fo, field, bad)
+        s = L.lbm_create(C.byref(g), 0.6, 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0, None, 0,
+                         C.byref(ctx))
+        assert s == P.LBM_ERR_ARG, field
+    # halo faces come in pairs; a slab cannot run the bulk-velocity controller
+    assert P.lbm_workspace_bytes(_grid(bc=(P.LBM_BC_HALO, 0, 1, 2, 0, 0)), 0, 1) == 0
+    gh = _grid(bc=(P.LBM_BC_HALO, P.LBM_BC_HALO, 1, 2, 0, 0))
+    assert P.lbm_workspace_bytes(gh, 0, 1) > 0
+    fo = P.LbmForcing()
+    fo.u_bulk_target, fo.ctrl_gain = 0.05, 0.01
+    s = L.lbm_create(C.byref(gh), 0.6, 0.1, P._DP(), C.byref(fo), 0, 1, 1, 0.0, None, 0,
+                     C.byref(ctx))
+    assert s == P.LBM_ERR_ARG
+    assert L.lbm_halo_bytes(None) == 0
+    assert L.lbm_halo_pack(None, None, None) == P.LBM_ERR_ARG
+    assert L.lbm_halo_unpack(None, None, None) == P.LBM_ERR_ARG
+    # the ensemble runs the default model on whole boxes
+    cases = W.ensemble_boxes(n_boxes=2, ny=16, nz=8, nx_range=(40, 90), seed=3)
+    for kw in ({"forcing_scheme": 1}, {"drag_streamwise_only": 1}, {"sgs_rho_power": 2}):
+        arr = (P.LbmBox * 2)()
+        keep = []
+        for i, c in enumerate(cases):
+            gg, ff, lad, k = P._case_inputs(c.replace(**kw) if i == 1 else c)
+            keep.append((k, lad))
+            arr[i].grid, arr[i].forcing, arr[i].tau0, arr[i].cs = gg, ff, c.tau0, c.cs
+            arr[i].lad = P._dp(lad) if lad is not None else P._DP()
+        assert P.lbm_batch_workspace_bytes(arr, P.LBM_F16_SHIFTED, 1) == 0, kw
+
+
 def test_null_context_calls_fail_cleanly():
     L = P.lib()
     assert L.lbm_step(None, 1) == P.LBM_ERR_ARG
@@ -103,9 +139,10 @@ def test_null_context_calls_fail_cleanly():
 
 
 def test_structs_match_the_header():
-    # lbm_grid: 9 int32; lbm_forcing: 3+1 doubles, 2 int32, 2+3 doubles, 1 pointer
+    # lbm_grid: 9 int32; lbm_forcing: 3+1 doubles, 2 int32, 2+3 doubles, 1 pointer,
+    # 4 int32 (model variants)
     assert C.sizeof(P.LbmGrid) == 36
-    assert C.sizeof(P.LbmForcing) == 8 * 4 + 8 + 8 * 5 + 8
+    assert C.sizeof(P.LbmForcing) == 8 * 4 + 8 + 8 * 5 + 8 + 16
 
 
 def test_ensemble_arguments_checked_without_a_device():

@@ -56,6 +56,27 @@ for i, c in enumerate(boxes):
     assert np.array_equal(bt.box(i).get_f(), alone.get_f()), c.name
     alone.close()
 bt.close()
+# the model variants and the halo data path under the same checks
+for c in (cases[2].replace(drag_streamwise_only=1, forcing_scheme=1, sgs_rho_power=2),
+          cases[6].replace(forcing_scheme=1)):
+    d, o = P.Domain(c), oracle.Oracle(c)
+    d.step(12)
+    o.step(12)
+    a, b = d.get_f(), o.get_f()
+    err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert err <= 1e-6, (c.name, "variant", err)
+    d.close()
+from paper_2206_15454_b300 import slabs as S
+c = W.channel_les(150, 9, 6).replace(u_bulk_target=0.0, ctrl_gain=0.0)
+whole = P.Domain(c)
+f0 = whole.get_f()
+whole.set_f(f0)
+sl = S.DeviceSlabs(c, 3)
+sl.set_f(f0)
+whole.step(12)
+sl.step(12)
+assert np.array_equal(sl.get_f(), whole.get_f()), "halo slabs differ"
+sl.doms[0].sync()
 print("checked build ok; worst FP32 rel L2", worst)
 '''
 
