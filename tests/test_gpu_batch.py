@@ -7,6 +7,7 @@ import pytest
 import oracle
 import paper_2206_15454_b300 as P
 import workloads as W
+from parity_util import assert_population_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -27,8 +28,7 @@ def test_batch_boxes_match_oracle_first_100_steps():
     for i, c in enumerate(cases):
         o = oracle.Oracle(c)
         o.step(100)
-        err = rel_l2(b.box(i).get_f(), o.get_f())
-        assert err <= 1e-6, (c.name, c.nx, err)
+        assert_population_parity(b.box(i).get_f(), o.get_f(), 1e-6, label=f"{c.name} nx={c.nx}")
 
 
 @pytest.mark.parametrize("storage", [P.LBM_F32, P.LBM_F16_SHIFTED])

@@ -2,8 +2,10 @@
 the same seeded inputs.
 
 Tolerances: FP32 compute with FP32 storage must keep the relative L2 error of
-the populations within 1e-6 over the first 100 steps; FP16/BF16 shifted
-storage errors are measured and bounded loosely (they are stated, not pinned).
+the populations within 1e-6 over the first 100 steps, and every single
+population within ELEM_TOL of the largest offset max |f - w| (parity_util
+derives the bound); FP16/BF16 shifted storage errors are measured and bounded
+loosely (they are stated, not pinned).
 """
 import math
 
@@ -14,6 +16,7 @@ import oracle
 import paper_2206_15454_b300 as P
 from paper_2206_15454_b300 import post
 import workloads as W
+from parity_util import assert_population_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -44,18 +47,19 @@ CASES = W.small_cases() + [
 @pytest.mark.parametrize("case", CASES, ids=[c.name for c in CASES])
 def test_initial_state_matches(case):
     d, o = pair(case)
-    err = rel_l2(d.get_f(), o.get_f())
-    assert err < 1e-7, err
+    # the FP64 initial state rounded once to FP32: half an ulp of each offset
+    assert_population_parity(d.get_f(), o.get_f(), 1e-7, 1e-6, label=f"{case.name} initial")
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c.name for c in CASES])
 def test_first_100_steps_f32(case):
     d, o = pair(case)
+    done = 0
     for k in (1, 9, 90):
         d.step(k)
         o.step(k)
-        err = rel_l2(d.get_f(), o.get_f())
-        assert err <= F32_TOL, (k, err)
+        done += k
+        assert_population_parity(d.get_f(), o.get_f(), F32_TOL, label=f"{case.name} step {done}")
     rho_d, u_d = d.macro()
     rho_o, u_o = o.macro()
     assert np.max(np.abs(rho_d - rho_o)) < 1e-6
@@ -150,8 +154,7 @@ def test_full_size_channel_step_matches_oracle():
     d, o = pair(case)
     d.step(2)
     o.step(2)
-    err = rel_l2(d.get_f(), o.get_f())
-    assert err < F32_TOL, err
+    assert_population_parity(d.get_f(), o.get_f(), F32_TOL, label="channel 256x128x128, 2 steps")
     gd, ubd = d.drive()
     go, ubo = o.drive()
     assert abs(ubd - ubo) < 2e-6 * abs(ubo)
@@ -269,8 +272,7 @@ def test_paper_abl_forest_cases_match_oracle(forest):
     o.stats_reset(True)
     d.step(40)
     o.step(40)
-    err = rel_l2(d.get_f(), o.get_f())
-    assert err <= F32_TOL, (forest, err)
+    assert_population_parity(d.get_f(), o.get_f(), F32_TOL, label=f"forest case {forest}")
     # the forest friction velocity of Sec. 5 (Reynolds stresses at y/h = 2)
     h = 20.0 / (400.0 / case.ny)
     us_d = post.friction_velocity(d.stats()[0], 2 * h)
@@ -308,5 +310,4 @@ def test_full_size_canopy_step_matches_oracle():
     o.step(2)
     fo = o.get_f()
     o.close()
-    err = rel_l2(d.get_f(), fo)
-    assert err < F32_TOL, err
+    assert_population_parity(d.get_f(), fo, F32_TOL, label="canopy 512x128x256, 2 steps")
