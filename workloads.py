@@ -149,6 +149,21 @@ def canopy_abl(nx=512, ny=128, nz=256, h=10.0, a=0.2, cd=0.15, canopy_x0=128,
                 u_profile=log_law_inflow(ny, u_inf))
 
 
+def canopy_turbulent(nx=96, ny=24, nz=96, h=8.0, a=0.5, g=3e-5, cd=0.15, tau0=0.5005,
+                     u0=0.03, perturb=0.3, seed=SEED_BASE + 5) -> Case:
+    """A turbulent canopy flow cheap enough for the FP64 oracle: periodic in x,
+    y and z, a dense canopy (LAD a below height h) in the lower third driven by a
+    uniform body force, so shear layers form at both canopy edges (the
+    inflection point of canopy flows, Sec. 5) and turn turbulent; initial
+    uniform streamwise velocity u0 with seeded perturbations of perturb * 0.05
+    per component.  Two runs that differ by rounding decorrelate within about
+    8000 steps."""
+    return Case("canopy_turbulent", nx, ny, nz, bc_y=(PERIODIC, PERIODIC), tau0=tau0, cs=0.1,
+                g=(g, 0.0, 0.0), cd=cd, canopy_x=(0, nx), seed=seed,
+                init_perturb=perturb * 0.05, lad=lad_constant(ny, a, h),
+                u_profile=np.full(ny, u0))
+
+
 def abl_forest(case: int = 1, nx: int = 160, ny: int = 64, nz: int = 128,
                u_top: float = 0.05, tau0: float = 0.501, xbin: int = 1) -> Case:
     """The paper's atmospheric boundary layer over a forest (Sec. 5): a
