@@ -97,7 +97,16 @@ typedef enum lbm_force_scheme {
 typedef enum lbm_storage {
     LBM_F32 = 0,        /* f_i - w_i in FP32: 152 bytes moved per lattice update */
     LBM_F16_SHIFTED = 1,  /* f_i - w_i in FP16 (round to nearest even): 76 B/LUP */
-    LBM_BF16_SHIFTED = 2  /* f_i - w_i in BF16 (round to nearest even): 76 B/LUP */
+    LBM_BF16_SHIFTED = 2, /* f_i - w_i in BF16 (round to nearest even): 76 B/LUP */
+    /* Or-ed into one of the above: AA-pattern in-place storage.  One population
+     * set (with a ghost layer one cell wide) instead of two, the same bytes per
+     * lattice update.  After an even number of steps f*_i(x) sits in slot
+     * opp(i) of cell x, after an odd number in slot i of cell x + c_i; steps
+     * alternate between the two and read and write each location from one
+     * thread.  Every boundary kind but LBM_BC_HALO, the model variants and the
+     * read-outs work as with two sets; not available: the learned correction
+     * (lbm_set_correction, lbm_features), ensembles, lbm_test_withhold_fill. */
+    LBM_STORAGE_AA = 0x100
 } lbm_storage;
 
 typedef struct lbm_grid {
@@ -133,8 +142,9 @@ typedef struct lbm_forcing {
     int32_t reserved;             /* must be 0 */
 } lbm_forcing;
 
-/* Bytes of device workspace lbm_create needs for this grid and storage;
- * 0 on invalid arguments. */
+/* Bytes of device workspace lbm_create needs for this grid and storage
+ * (an lbm_storage value, optionally or-ed with LBM_STORAGE_AA); 0 on invalid
+ * arguments. */
 size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t storage, int32_t stats_xbins);
 
 /* Create a domain and initialise it on the device to f = f_eq(1, u0) with

@@ -23,8 +23,12 @@ LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK, LBM_BC_FREESLIP, LBM_BC_EQUILIBRIUM, LBM_BC_
     LBM_BC_OUTFLOW, LBM_BC_HALO = range(7)
 LBM_FORCE_GUO, LBM_FORCE_EXACT_DIFFERENCE = range(2)
 LBM_F32, LBM_F16_SHIFTED, LBM_BF16_SHIFTED = range(3)
-STORAGE_NAMES = {"f32": LBM_F32, "f16s": LBM_F16_SHIFTED, "bf16s": LBM_BF16_SHIFTED}
-BYTES_PER_LUP = {LBM_F32: 152, LBM_F16_SHIFTED: 76, LBM_BF16_SHIFTED: 76}
+LBM_STORAGE_AA = 0x100  # or-ed into a storage type: AA-pattern in-place storage (one set)
+STORAGE_NAMES = {"f32": LBM_F32, "f16s": LBM_F16_SHIFTED, "bf16s": LBM_BF16_SHIFTED,
+                 "f32-aa": LBM_F32 | LBM_STORAGE_AA, "f16s-aa": LBM_F16_SHIFTED | LBM_STORAGE_AA,
+                 "bf16s-aa": LBM_BF16_SHIFTED | LBM_STORAGE_AA}
+_BYTES = {LBM_F32: 152, LBM_F16_SHIFTED: 76, LBM_BF16_SHIFTED: 76}
+BYTES_PER_LUP = {k: _BYTES[k & 0xFF] for k in STORAGE_NAMES.values()}
 
 
 class LbmGrid(C.Structure):

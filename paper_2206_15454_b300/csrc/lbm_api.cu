@@ -33,7 +33,30 @@ constexpr int kMassBlocks = 1024;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-size_t elem_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
+size_t elem_bytes(int storage) { return (storage & 0xff) == LBM_F32 ? 4 : 2; }
+
+// storage argument: an element type, or-ed with LBM_STORAGE_AA for the
+// AA-pattern layout (one population set)
+bool storage_ok(int32_t storage) {
+  const int t = storage & 0xff, flags = storage & ~0xff;
+  return t >= 0 && t <= 2 && (flags == 0 || flags == LBM_STORAGE_AA);
+}
+bool is_aa(int32_t storage) { return (storage & LBM_STORAGE_AA) != 0; }
+
+// AA-pattern set: rows of nx + 2 cells rounded up to whole 128-byte lines (the
+// left ghost of a row is the previous row's last slot), planes [q][z][y] with
+// a ghost layer in y and z, one line before the first row.
+struct AAShape {
+  long long pitch, lead, elems;
+};
+AAShape aa_shape_of(const lbm_grid& g, int storage) {
+  const long long line = 128 / (long long)elem_bytes(storage);
+  AAShape a;
+  a.pitch = (g.nx + 2 + line - 1) / line * line;
+  a.lead = line;
+  a.elems = a.lead + (long long)NQ * (g.nz + 2) * (g.ny + 2) * a.pitch + line;
+  return a;
+}
 
 // chunk width: the smallest of 64, 128, 256 cells that covers a row, else 256
 int chunk_width(int nx) { return nx <= 64 ? 64 : (nx <= 128 ? 128 : 256); }
@@ -64,8 +87,9 @@ struct Layout {
 Layout layout_of(const lbm_grid& g, int storage, int nbins, int xt = 0) {
   Layout L;
   const Shape s = shape_of(g, storage, xt);
-  L.f_bytes = align_up((size_t)s.elems * elem_bytes(storage), kAlign);
-  size_t off = 2 * L.f_bytes;
+  const long long elems = is_aa(storage) ? aa_shape_of(g, storage).elems : s.elems;
+  L.f_bytes = align_up((size_t)elems * elem_bytes(storage), kAlign);
+  size_t off = is_aa(storage) ? L.f_bytes : 2 * L.f_bytes;  // AA: one set
   L.stats_off = off;  off += align_up(sizeof(double) * 9 * nbins * g.ny, kAlign);
   L.state_off = off;  off += align_up(sizeof(DevState), kAlign);
   L.ubpart_off = off; off += align_up(sizeof(long long) * 2 * MAX_BLOCKS, kAlign);
@@ -98,7 +122,9 @@ bool grid_ok(const lbm_grid* g) {
 
 struct lbm_ctx {
   lbm_grid grid;
-  int storage = 0, nbins = 1;
+  int storage = 0, nbins = 1;   // element type (lbm_storage without flags)
+  bool aa = false;              // AA-pattern layout: one population set
+  AAShape ash{};
   double tau0 = 0, cs = 0;
   lbm_forcing forcing;
   std::vector<double> lad, uprof;
@@ -145,11 +171,20 @@ struct lbm_ctx {
   float* feq_in() const { return reinterpret_cast<float*>(ws + L.feqin_off); }
   double* uprof_dev() const { return reinterpret_cast<double*>(ws + L.uprof_off); }
   double* mass_buf() const { return reinterpret_cast<double*>(ws + L.mass_off); }
-  // device element index of population q at cell (x, y, z)
+  // device element index of the post-collision population q at cell (x, y, z)
+  // of the current state (AA: in the layout of the current step parity)
   long long dev_index(int q, int x, int y, int z) const {
+    if (aa) {
+      auto at = [&](int qq, int xx, int yy, int zz) {
+        return ash.lead + (((long long)qq * (grid.nz + 2) + (zz + 1)) * (grid.ny + 2) + (yy + 1)) * ash.pitch + xx;
+      };
+      return (steps & 1) == 0 ? at(opp(q), x, y, z) : at(q, x + cx(q), y + cy(q), z + cz(q));
+    }
     return (((long long)y * grid.nz + z) * sh.nxc + x / sh.xt) * sh.row + (long long)q * sh.xtp +
            sh.g + x % sh.xt;
   }
+  // elements of one population set
+  long long set_elems() const { return aa ? ash.elems : sh.elems; }
 };
 
 // A correction network: parameters and training state on the device.
@@ -283,10 +318,32 @@ StepParams make_params(const lbm_ctx* c) {
   p.drag_x_only = c->forcing.drag_streamwise_only;
   p.edm = c->forcing.scheme == LBM_FORCE_EXACT_DIFFERENCE;
   p.tau_rho2 = c->forcing.sgs_rho_power == 2;
+  p.aa_pitch = c->ash.pitch;
+  p.aa_lead = c->ash.lead;
+  p.aa_elems = c->aa ? c->ash.elems : 0;
+  p.aa_parity = (int)(c->steps & 1);
+  if (c->aa) {
+    // the bulk-velocity sums rotate through three slots (written, read,
+    // cleared for the next step)
+    p.slot_write = (int)(c->steps % 3);
+    p.slot_read = (int)((c->steps + 2) % 3);
+  }
   p.state = c->state();
-  p.src = c->fbuf(c->cur);
-  p.dst = c->fbuf(1 - c->cur);
+  if (c->aa) {
+    p.src = p.dst = c->fbuf(0);  // one set, read and written in place
+  } else {
+    p.src = c->fbuf(c->cur);
+    p.dst = c->fbuf(1 - c->cur);
+  }
   return p;
+}
+
+// Instantiate a functor over the storage type (AA-pattern kernels).
+template <typename Fn>
+void dispatch_s(const lbm_ctx* c, Fn&& fn) {
+  if (c->storage == LBM_F32) fn(std::integral_constant<int, 0>());
+  else if (c->storage == LBM_F16_SHIFTED) fn(std::integral_constant<int, 1>());
+  else fn(std::integral_constant<int, 2>());
 }
 
 // Instantiate a functor over (chunk width, storage type).
@@ -316,21 +373,44 @@ void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
                     uses_variant(c->forcing), true);
 }
 
-// Shared-memory stages: as many tiles in flight as fit beside three blocks
-// per SM and their static shared memory (about 12 KB with statistics): at
-// most 8, at least 2.
+// Launch shape and shared-memory stages of a step kernel form: a chunk of XT
+// cells per tile row with cpt cells per thread, 256 cpt / XT rows (consecutive
+// z) per tile; as many tiles in flight as fit beside the form's blocks per SM
+// (three of one cell per thread, two of two) and their static shared memory
+// (about 12 KB with statistics): at most 8, at least 2.
+struct StagePlan {
+  dim3 block;
+  int nstage;
+  size_t smem;
+};
 template <int XT, int S>
-void plan_stages(lbm_ctx* c) {
+StagePlan stage_plan(int cpt) {
   using St = Stage<XT, S>;
-  const size_t stage = (size_t)c->block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
-  c->nstage = (int)std::max<size_t>(2, std::min<size_t>(8, (62 * 1024) / stage));
-  c->stage_smem = c->nstage * stage;
-  Kern<XT, S>::configure(c->stage_smem);
+  StagePlan sp;
+  sp.block = dim3(XT / cpt, 256 * cpt / XT, 1);
+  const size_t stage = (size_t)sp.block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
+  const size_t budget = cpt == 1 ? 62 * 1024 : 100 * 1024;
+  sp.nstage = (int)std::max<size_t>(2, std::min<size_t>(8, budget / stage));
+  sp.smem = sp.nstage * stage;
+  return sp;
 }
 
 template <int XT, int S>
-int occupancy(dim3 block, size_t smem) {
-  return Kern<XT, S>::occupancy(block, smem);
+void plan_stages(lbm_ctx* c) {
+  const bool var = uses_variant(c->forcing);
+  const StagePlan def = stage_plan<XT, S>(Kern<XT, S>::cells_per_thread(false));
+  const StagePlan vf = stage_plan<XT, S>(Kern<XT, S>::cells_per_thread(true));
+  Kern<XT, S>::configure(def.smem, vf.smem);  // per form: the same for every context
+  const StagePlan& own = var ? vf : def;
+  c->block = own.block;
+  c->nstage = own.nstage;
+  c->stage_smem = own.smem;
+  c->nzg = (c->grid.nz + (int)c->block.y - 1) / (int)c->block.y;
+}
+
+template <int XT, int S>
+int occupancy(const lbm_ctx* c) {
+  return Kern<XT, S>::occupancy(c->block, c->stage_smem, uses_variant(c->forcing));
 }
 
 // Ghost slots of both population sets from their cells: the current set
@@ -366,6 +446,14 @@ void launch_mass(const lbm_ctx* c) {
 template <int XT, int S>
 void launch_macro(const lbm_ctx* c, const StepParams& p, float* out) {
   Kern<XT, S>::macro(c->sm_count * 8, c->stream, p, out);
+}
+
+// The density and velocity the next step computes, in either layout.
+void launch_macro_any(const lbm_ctx* c, const StepParams& p, float* out) {
+  if (c->aa)
+    dispatch_s(c, [&](auto s) { KernAA<decltype(s)::value>::macro(c->sm_count * 8, c->stream, p, out); });
+  else
+    dispatch(c, [&](auto xt, auto s) { launch_macro<decltype(xt)::value, decltype(s)::value>(c, p, out); });
 }
 
 // The correction's inputs over all first-cell columns into X, and with th
@@ -431,9 +519,10 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) 
 extern "C" {
 
 size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t storage, int32_t stats_xbins) {
-  if (!grid_ok(grid) || storage < 0 || storage > 2 || stats_xbins < 1 ||
+  if (!grid_ok(grid) || !storage_ok(storage) || stats_xbins < 1 ||
       stats_xbins > MAX_XBINS || stats_xbins > grid->nx)
     return 0;
+  if (is_aa(storage) && grid->x_lo == LBM_BC_HALO) return 0;  // slabs use the pull layout
   return layout_of(*grid, storage, stats_xbins).total;
 }
 
@@ -469,7 +558,9 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
   lbm_ctx* c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ERR_OOM;
   c->grid = *grid;
-  c->storage = storage;
+  c->storage = storage & 0xff;
+  c->aa = is_aa(storage);
+  c->ash = aa_shape_of(*grid, storage);
   c->nbins = stats_xbins;
   c->tau0 = tau0;
   c->cs = cs;
@@ -480,7 +571,7 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
   if (forcing->u_in_profile) c->uprof.assign(forcing->u_in_profile, forcing->u_in_profile + grid->ny);
   c->seed = seed;
   c->init_perturb = init_perturb;
-  c->sh = shape_of(*grid, storage, xt);
+  c->sh = shape_of(*grid, storage & 0xff, xt);
   c->cells = (long long)grid->nx * grid->ny * grid->nz;
   c->L = layout_of(*grid, storage, stats_xbins, xt);
   c->stream = stream;
@@ -506,13 +597,15 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
     c->owns_ws = true;
   }
 
-  // launch shape: a chunk of XT cells per row, 256 / XT rows (consecutive z) per block
-  c->block = dim3(c->sh.xt, 256 / c->sh.xt, 1);
-  c->nzg = (grid->nz + (int)c->block.y - 1) / (int)c->block.y;
-  dispatch(c, [&](auto xt, auto s) {
-    plan_stages<decltype(xt)::value, decltype(s)::value>(c);
-    c->blocks_per_sm = occupancy<decltype(xt)::value, decltype(s)::value>(c->block, c->stage_smem);
-  });
+  // launch shape and stages (plan_stages): per chunk width, storage and model form
+  if (c->aa) {
+    dispatch_s(c, [&](auto s) { c->blocks_per_sm = KernAA<decltype(s)::value>::occupancy(); });
+  } else {
+    dispatch(c, [&](auto xt, auto s) {
+      plan_stages<decltype(xt)::value, decltype(s)::value>(c);
+      c->blocks_per_sm = occupancy<decltype(xt)::value, decltype(s)::value>(c);
+    });
+  }
   if (cudaGetLastError() != cudaSuccess) return bail(LBM_ERR_CUDA);
 
   // boundary tables and inputs
@@ -535,7 +628,17 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
       cudaMemcpyAsync(c->uprof_dev(), c->uprof.data(), sizeof(double) * grid->ny,
                       cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     return bail(LBM_ERR_CUDA);
-  dispatch(c, [&](auto xt, auto s) { launch_init<decltype(xt)::value, decltype(s)::value>(c); });
+  if (c->aa) {
+    InitParams ip{};
+    ip.nx = grid->nx; ip.ny = grid->ny; ip.nz = grid->nz;
+    ip.u_prof = c->uprof_dev();
+    ip.seed = c->seed;
+    ip.amp = c->init_perturb;
+    const StepParams p = make_params(c);
+    dispatch_s(c, [&](auto s) { KernAA<decltype(s)::value>::init(c->sm_count * 8, c->stream, p, ip); });
+  } else {
+    dispatch(c, [&](auto xt, auto s) { launch_init<decltype(xt)::value, decltype(s)::value>(c); });
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(LBM_ERR_CUDA);
   *out = c;
@@ -560,9 +663,54 @@ lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
   return LBM_OK;
 }
 
+namespace {
+// The launch of one AA step: the boundary fill, then step B (from the
+// swapped layout) or A (from the streamed one) with its read and write
+// offsets relative to the cell's slot of direction 0.
+lbm_status aa_step(lbm_ctx* c) {
+  const StepParams p = make_params(c);
+  const lbm_grid& g = c->grid;
+  const long long faces = 2ll * ((long long)g.ny * g.nz + (long long)g.nx * g.nz + (long long)g.nx * g.ny);
+  const int fblocks = (int)std::max<long long>(1, std::min<long long>((faces + 255) / 256, c->sm_count * 8ll));
+  AAStep a;
+  a.p = p;
+  const long long ys = c->ash.pitch, zs = (g.ny + 2) * ys, qs = (g.nz + 2) * zs;
+  for (int i = 0; i < NQ; i++) {
+    const long long own = (long long)i * qs, rev = (long long)opp(i) * qs;
+    const long long shift = (long long)cz(i) * zs + (long long)cy(i) * ys + cx(i);
+    if (p.aa_parity == 0) {  // B
+      a.rd[i] = rev - shift;
+      a.wr[i] = own + shift;
+    } else {  // A
+      a.rd[i] = own;
+      a.wr[i] = rev;
+    }
+  }
+  a.nxc = (g.nx + AA_XT - 1) / AA_XT;
+  a.nzg = (g.nz + AA_ZR - 1) / AA_ZR;
+  a.nunit = a.nxc * a.nzg * g.ny;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(a.nunit, (long long)c->sm_count * c->blocks_per_sm));
+  dispatch_s(c, [&](auto s) {
+    KernAA<decltype(s)::value>::fill(fblocks, c->stream, p);
+    KernAA<decltype(s)::value>::step(grid, c->stream, a, c->stats_on, uses_variant(c->forcing));
+  });
+  CK(c, cudaGetLastError());
+  c->steps++;
+  if (c->stats_on) c->stats_samples++;
+  return LBM_OK;
+}
+}  // namespace
+
 lbm_status lbm_step(lbm_ctx* c, int32_t n) {
   READY(c);
   if (n < 0) return arg_error(c, "lbm_step: n < 0");
+  if (c->aa) {
+    for (int32_t k = 0; k < n; k++) {
+      const lbm_status s = aa_step(c);
+      if (s != LBM_OK) return s;
+    }
+    return LBM_OK;
+  }
   for (int32_t k = 0; k < n; k++) {
     const StepParams p = make_params(c);
     dispatch(c, [&](auto xt, auto s) {
@@ -586,6 +734,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
 lbm_status lbm_test_withhold_fill(lbm_ctx* c, int32_t fill) {
   READY(c);
   if (fill < 0) return arg_error(c, "lbm_test_withhold_fill: fill < 0");
+  if (c->aa) return arg_error(c, "lbm_test_withhold_fill: the AA layout has no tile fills");
   c->test_withhold = fill;
   return LBM_OK;
 }
@@ -703,7 +852,14 @@ lbm_status lbm_stats_end(lbm_ctx* c, double* out, size_t n, int64_t* samples) {
 lbm_status lbm_mass(lbm_ctx* c, double* out) {
   READY(c);
   if (!out) return arg_error(c, "lbm_mass: out is NULL");
-  dispatch(c, [&](auto xt, auto s) { launch_mass<decltype(xt)::value, decltype(s)::value>(c); });
+  if (c->aa) {
+    const StepParams p = make_params(c);
+    dispatch_s(c, [&](auto s) { KernAA<decltype(s)::value>::mass(kMassBlocks, c->stream, p, c->mass_buf()); });
+    mass_final_kernel<<<1, 32, 0, c->stream>>>(c->mass_buf(), kMassBlocks, (double)c->cells,
+                                                c->mass_buf() + kMassBlocks);
+  } else {
+    dispatch(c, [&](auto xt, auto s) { launch_mass<decltype(xt)::value, decltype(s)::value>(c); });
+  }
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
@@ -717,7 +873,7 @@ lbm_status lbm_get_f(lbm_ctx* c, double* host, size_t n) {
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
   const size_t eb = elem_bytes(c->storage);
-  std::vector<unsigned char> raw((size_t)c->sh.elems * eb);
+  std::vector<unsigned char> raw((size_t)c->set_elems() * eb);
   CK(c, cudaMemcpy(raw.data(), c->fbuf(c->cur), raw.size(), cudaMemcpyDeviceToHost));
   const lbm_grid& g = c->grid;
   for (int i = 0; i < NQ; i++)
@@ -740,7 +896,7 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* host, size_t n) {
   if (!host || n != (size_t)NQ * c->cells) return arg_error(c, "lbm_set_f: wrong size");
   CK(c, cudaStreamSynchronize(c->stream));
   const size_t eb = elem_bytes(c->storage);
-  std::vector<unsigned char> raw((size_t)c->sh.elems * eb, 0);
+  std::vector<unsigned char> raw((size_t)c->set_elems() * eb, 0);
   const lbm_grid& g = c->grid;
   for (int i = 0; i < NQ; i++)
     for (int z = 0; z < g.nz; z++)
@@ -754,7 +910,9 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* host, size_t n) {
           else reinterpret_cast<__nv_bfloat16*>(raw.data())[dk] = Store<2>::from_double(v);
         }
   CK(c, cudaMemcpy(c->fbuf(c->cur), raw.data(), raw.size(), cudaMemcpyHostToDevice));
-  dispatch(c, [&](auto xt, auto s) { launch_ghosts<decltype(xt)::value, decltype(s)::value>(c); });
+  // (AA: the slots a step reads from outside the domain are filled before each step)
+  if (!c->aa)
+    dispatch(c, [&](auto xt, auto s) { launch_ghosts<decltype(xt)::value, decltype(s)::value>(c); });
   CK(c, cudaGetLastError());
   CK(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
@@ -771,9 +929,7 @@ lbm_status lbm_get_macro(lbm_ctx* c, double* rho, double* u, size_t n) {
     }
   }
   const StepParams p = make_params(c);
-  dispatch(c, [&](auto xt, auto s) {
-    launch_macro<decltype(xt)::value, decltype(s)::value>(c, p, c->macro_buf);
-  });
+  launch_macro_any(c, p, c->macro_buf);
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
@@ -795,9 +951,7 @@ lbm_status lbm_get_q(lbm_ctx* c, double* q, size_t n) {
     }
   }
   const StepParams p = make_params(c);
-  dispatch(c, [&](auto xt, auto s) {
-    launch_macro<decltype(xt)::value, decltype(s)::value>(c, p, c->macro_buf);
-  });
+  launch_macro_any(c, p, c->macro_buf);
   // Q into the density plane of the field buffer (the kernel reads the velocity planes only)
   const lbm_grid& g = c->grid;
   q_kernel<<<c->sm_count * 8, 256, 0, c->stream>>>(c->macro_buf + c->cells, c->macro_buf, g.nx,
@@ -818,7 +972,12 @@ lbm_status lbm_drive(lbm_ctx* c, double g[3], double* u_bulk) {
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
   double ub = 0.0;
-  if (c->steps > 0) {
+  if (c->steps > 0 && c->aa) {  // one exact sum per step, three slots in rotation
+    long long sum = 0;
+    CK(c, cudaMemcpy(&sum, c->ub_part() + (size_t)((c->steps + 2) % 3), sizeof(long long),
+                     cudaMemcpyDeviceToHost));
+    ub = (double)sum / 4294967296.0 / (double)c->cells;
+  } else if (c->steps > 0) {
     std::vector<long long> part(c->last_grid);
     CK(c, cudaMemcpy(part.data(), c->ub_part() + (size_t)((c->steps + 1) % 2) * MAX_BLOCKS,
                      sizeof(long long) * part.size(), cudaMemcpyDeviceToHost));
@@ -885,7 +1044,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   if (!path) return arg_error(c, "lbm_save: path is NULL");
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
-  const size_t fb = (size_t)c->sh.elems * elem_bytes(c->storage);
+  const size_t fb = (size_t)c->set_elems() * elem_bytes(c->storage);
   const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
   const size_t ub = sizeof(long long) * 2 * MAX_BLOCKS;
   std::vector<unsigned char> payload(fb + sb + ub);
@@ -896,7 +1055,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "LBMB300\0", 8);
   h.version = 3;
-  h.storage = c->storage;
+  h.storage = c->storage | (c->aa ? LBM_STORAGE_AA : 0);
   h.nbins = c->nbins;
   h.grid = c->grid;
   h.steps = c->steps;
@@ -929,12 +1088,13 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     return LBM_ERR_IO;
   }
   CkptHeader h;
-  const size_t fb = (size_t)c->sh.elems * elem_bytes(c->storage);
+  const size_t fb = (size_t)c->set_elems() * elem_bytes(c->storage);
   const size_t sb = sizeof(double) * 9 * c->nbins * c->grid.ny;
   const size_t ub = sizeof(long long) * 2 * MAX_BLOCKS;
   std::vector<unsigned char> payload;
   bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, "LBMB300\0", 8) == 0 &&
-            h.version == 3 && h.storage == c->storage && h.nbins == c->nbins &&
+            h.version == 3 && h.storage == (c->storage | (c->aa ? LBM_STORAGE_AA : 0)) &&
+            h.nbins == c->nbins &&
             std::memcmp(&h.grid, &c->grid, sizeof(lbm_grid)) == 0 &&
             h.payload_bytes == fb + sb + ub && h.last_grid >= 0 && h.last_grid <= MAX_BLOCKS;
   if (ok) {
@@ -996,9 +1156,12 @@ lbm_status lbm_get_macro_noalloc(lbm_ctx* c, double* rho, double* u, size_t n) {
     g_noalloc_ptr[dev].store(buf);
   }
   const StepParams p = make_params(c);
-  dispatch(c, [&](auto xt, auto s) {
-    Kern<decltype(xt)::value, decltype(s)::value>::macro_d(c->sm_count * 8, c->stream, p, buf);
-  });
+  if (c->aa)
+    dispatch_s(c, [&](auto s) { KernAA<decltype(s)::value>::macro_d(c->sm_count * 8, c->stream, p, buf); });
+  else
+    dispatch(c, [&](auto xt, auto s) {
+      Kern<decltype(xt)::value, decltype(s)::value>::macro_d(c->sm_count * 8, c->stream, p, buf);
+    });
   CK(c, cudaGetLastError());
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
@@ -1691,6 +1854,7 @@ const char* lbm_mlp_last_error(const lbm_mlp* m) { return m ? m->err.c_str() : "
 lbm_status lbm_set_correction(lbm_ctx* c, const lbm_mlp* m, double lam) {
   READY(c);
   if (c->batch) return arg_error(c, "lbm_set_correction: not available for ensemble boxes");
+  if (c->aa) return arg_error(c, "lbm_set_correction: not available with the AA layout");
   if (m && c->grid.ny < 3) return arg_error(c, "lbm_set_correction: needs ny >= 3");
   if (!std::isfinite(lam)) return arg_error(c, "lbm_set_correction: lam not finite");
   if (m) {
@@ -1711,6 +1875,7 @@ lbm_status lbm_features(lbm_ctx* c, float* X, size_t n) {
   READY(c);
   const size_t cols = (size_t)c->grid.nx * c->grid.nz;
   if (!X || n != cols * MLP_IN) return arg_error(c, "lbm_features: wrong size");
+  if (c->aa) return arg_error(c, "lbm_features: not available with the AA layout");
   if (c->grid.ny < 3) return arg_error(c, "lbm_features: needs ny >= 3");
   lbm_status s0 = ensure_feat_buf(c);
   if (s0 != LBM_OK) return s0;

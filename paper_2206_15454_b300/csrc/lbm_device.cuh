@@ -49,12 +49,16 @@ __host__ __device__ constexpr double wgt_d(int i) {
 
 // ---- storage types ----------------------------------------------------------
 template <int S> struct Store;
+// ld2 / st2: two adjacent values at a 4-byte aligned address (16-bit types:
+// one 32-bit access), rounded to nearest like st.
 template <> struct Store<0> {
   using T = float;
   static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
   static __device__ __forceinline__ float to_float(T v) { return v; }
   static __device__ __forceinline__ void st(T* p, float v) { *p = v; }
   static __host__ __device__ __forceinline__ T from_double(double v) { return (float)v; }
+  static __device__ __forceinline__ float2 ld2(const T* p) { return make_float2(p[0], p[1]); }
+  static __device__ __forceinline__ void st2(T* p, float2 v) { p[0] = v.x; p[1] = v.y; }
 };
 template <> struct Store<1> {
   using T = __half;
@@ -62,6 +66,12 @@ template <> struct Store<1> {
   static __device__ __forceinline__ float to_float(T v) { return __half2float(v); }
   static __device__ __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v); }
   static __host__ __device__ __forceinline__ T from_double(double v) { return __double2half(v); }
+  static __device__ __forceinline__ float2 ld2(const T* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+  }
+  static __device__ __forceinline__ void st2(T* p, float2 v) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.x, v.y);
+  }
 };
 template <> struct Store<2> {
   using T = __nv_bfloat16;
@@ -69,6 +79,12 @@ template <> struct Store<2> {
   static __device__ __forceinline__ float to_float(T v) { return __bfloat162float(v); }
   static __device__ __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
   static __host__ __device__ __forceinline__ T from_double(double v) { return __double2bfloat16(v); }
+  static __device__ __forceinline__ float2 ld2(const T* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
+  static __device__ __forceinline__ void st2(T* p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+  }
 };
 
 // ---- device-resident controller / health state --------------------------------
@@ -168,6 +184,11 @@ struct StepParams {
   // bodyforce), Q^1/2 / rho^2 under the root of tau_total (the tau_total
   // equation as printed) instead of / rho (Eq. strain solved for tau)
   int drag_x_only, edm, tau_rho2;
+  // AA-pattern storage (one population set, lbm_aa.cuh): row pitch and lead
+  // of the set in elements, and the layout of the current state (0 swapped,
+  // after an even number of steps; 1 streamed)
+  long long aa_pitch, aa_lead, aa_elems;  // aa_elems: elements of the set (checked builds)
+  int aa_parity;
 };
 
 // x boundary modes of StepParams::x_io
@@ -421,6 +442,160 @@ __device__ __forceinline__ void collide_edm(const float* f, const Macro& m, floa
     const float odd = om * (w * r3 * ei) + w * r3 * hi;
     emit(i, keep * f[i] + (even + odd));
     emit(i + 1, keep * f[i + 1] + (even - odd));
+  }
+}
+
+// ---- the default model's collision on one cell (float) or two (float2) ---------------
+// Written once with explicit round-to-nearest operations (no contraction left
+// to the compiler), so one cell per thread (scalar instructions) and two cells
+// per thread (packed FP32x2 instructions: FFMA2, FADD2, FMUL2) give
+// bit-identical results.  Division and square root are the same per-component
+// approximations (-prec-div=false, -prec-sqrt=false) in both.
+template <class V>
+struct VOps;
+template <>
+struct VOps<float> {
+  static __device__ __forceinline__ float c(float a) { return a; }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float d) { return __fmaf_rn(a, b, d); }
+  static __device__ __forceinline__ float neg(float a) { return -a; }
+  static __device__ __forceinline__ float div(float a, float b) { return a / b; }
+  static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
+  // a where k > 0, else b
+  static __device__ __forceinline__ float where_pos(float k, float a, float b) { return k > 0.f ? a : b; }
+};
+template <>
+struct VOps<float2> {
+  static __device__ __forceinline__ float2 c(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, neg(b)); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 d) { return __ffma2_rn(a, b, d); }
+  static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+  static __device__ __forceinline__ float2 div(float2 a, float2 b) { return make_float2(a.x / b.x, a.y / b.y); }
+  static __device__ __forceinline__ float2 sqrt(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+  static __device__ __forceinline__ float2 where_pos(float2 k, float2 a, float2 b) {
+    return make_float2(k.x > 0.f ? a.x : b.x, k.y > 0.f ? a.y : b.y);
+  }
+};
+
+template <class V>
+struct MacroV {
+  V drho, rho, ux, uy, uz, Fx, Fy, Fz;
+};
+
+// Eqs. density and momentum with the driving acceleration and the canopy
+// drag solved jointly (as moments()).  k: C_D a(y) per cell; a cell with
+// k = 0 keeps u and F as without drag (selected, so two cells side by side
+// give what each gives alone).
+template <class V>
+__device__ __forceinline__ MacroV<V> moments_v(const V* f, V gx, V gy, V gz, V k, bool any_drag) {
+  using O = VOps<V>;
+  V sm[NQ], df[NQ];
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    sm[i] = O::add(f[i], f[i + 1]);
+    df[i] = O::sub(f[i], f[i + 1]);
+  }
+  V drho = f[0];
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) drho = O::add(drho, sm[i]);
+  // odd directions 1 (+x), 3 (+y), 5 (+z), 7 (+x+y), 9 (+x-y), 11 (+x+z),
+  // 13 (+x-z), 15 (+y+z), 17 (+y-z)
+  const V mx = O::add(O::add(O::add(O::add(df[1], df[7]), df[9]), df[11]), df[13]);
+  const V my = O::add(O::add(O::sub(O::add(df[3], df[7]), df[9]), df[15]), df[17]);
+  const V mz = O::sub(O::add(O::sub(O::add(df[5], df[11]), df[13]), df[15]), df[17]);
+  MacroV<V> m;
+  m.drho = drho;
+  m.rho = O::add(O::c(1.0f), drho);
+  const V inv_rho = O::div(O::c(1.0f), m.rho);
+  const V hr = O::mul(O::c(0.5f), m.rho);
+  V vx = O::mul(O::fma(hr, gx, mx), inv_rho);
+  V vy = O::mul(O::fma(hr, gy, my), inv_rho);
+  V vz = O::mul(O::fma(hr, gz, mz), inv_rho);
+  m.Fx = O::mul(m.rho, gx);
+  m.Fy = O::mul(m.rho, gy);
+  m.Fz = O::mul(m.rho, gz);
+  if (any_drag) {
+    // g_c = -k |u| u with u = v + g_c/2: u parallel to v, |u| = s |v|,
+    // s = 2 / (1 + sqrt(1 + 2 k |v|)) (s = 1 where k = 0)
+    const V vn = O::sqrt(O::fma(vx, vx, O::fma(vy, vy, O::mul(vz, vz))));
+    const V s = O::div(O::c(2.0f), O::add(O::c(1.0f), O::sqrt(O::fma(O::mul(O::c(2.0f), k), vn, O::c(1.0f)))));
+    const V ux = O::mul(vx, s), uy = O::mul(vy, s), uz = O::mul(vz, s);
+    const V rk = O::neg(O::mul(m.rho, O::mul(O::mul(k, s), vn)));  // -rho k |u|
+    m.Fx = O::where_pos(k, O::fma(rk, ux, m.Fx), m.Fx);
+    m.Fy = O::where_pos(k, O::fma(rk, uy, m.Fy), m.Fy);
+    m.Fz = O::where_pos(k, O::fma(rk, uz, m.Fz), m.Fz);
+    vx = O::where_pos(k, ux, vx);
+    vy = O::where_pos(k, uy, vy);
+    vz = O::where_pos(k, uz, vz);
+  }
+  m.ux = vx;
+  m.uy = vy;
+  m.uz = vz;
+  return m;
+}
+
+// BGK-Smagorinsky collision with Guo forcing (as collide()), per pair
+// (i, i+1) from the even and odd parts of f_eq and of the forcing term.
+// c_i . a for the odd direction i of a pair, from the components of a
+template <class V>
+__device__ __forceinline__ V pair_dot(int i, V ax, V ay, V az) {
+  using O = VOps<V>;
+  return i == 1 ? ax : i == 3 ? ay : i == 5 ? az : i == 7 ? O::add(ax, ay) : i == 9 ? O::sub(ax, ay)
+       : i == 11 ? O::add(ax, az) : i == 13 ? O::sub(ax, az) : i == 15 ? O::add(ay, az)
+       : O::sub(ay, az);
+}
+
+template <class V, class Emit>
+__device__ __forceinline__ void collide_v(const V* f, const MacroV<V>& m, float tau0, float c18,
+                                          Emit&& emit) {
+  using O = VOps<V>;
+  const V ux = m.ux, uy = m.uy, uz = m.uz;
+  const V uu = O::fma(ux, ux, O::fma(uy, uy, O::mul(uz, uz)));
+  const V base = O::fma(O::mul(O::c(-1.5f), m.rho), uu, m.drho);  // drho - 1.5 rho u.u
+  const V r45 = O::mul(O::c(4.5f), m.rho);
+  const V r3 = O::mul(O::c(3.0f), m.rho);
+  V pxx, pyy, pzz, pxy, pxz, pyz;  // Pi_neq (Eq. tensor) from the pair sums, summed in i order
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    const V e = pair_dot<V>(i, ux, uy, uz);
+    const V sym = O::mul(O::c(wgt(i)), O::fma(O::mul(r45, e), e, base));  // even part of f_eq - w
+    const V np = O::fma(O::c(-2.0f), sym, O::add(f[i], f[i + 1]));  // pair sum of f - f_eq
+    if (i == 1) pxx = np; else if (cx(i) != 0) pxx = O::add(pxx, np);
+    if (i == 3) pyy = np; else if (cy(i) != 0) pyy = O::add(pyy, np);
+    if (i == 5) pzz = np; else if (cz(i) != 0) pzz = O::add(pzz, np);
+    if (i == 7) pxy = np;
+    if (i == 9) pxy = O::sub(pxy, np);
+    if (i == 11) pxz = np;
+    if (i == 13) pxz = O::sub(pxz, np);
+    if (i == 15) pyz = np;
+    if (i == 17) pyz = O::sub(pyz, np);
+  }
+  const V off = O::fma(pxy, pxy, O::fma(pxz, pxz, O::mul(pyz, pyz)));
+  const V q2 = O::fma(pxx, pxx, O::fma(pyy, pyy, O::fma(pzz, pzz, O::mul(O::c(2.0f), off))));
+  const V arg = O::add(O::c(tau0 * tau0), O::div(O::mul(O::c(c18), O::sqrt(q2)), m.rho));
+  const V tau = O::mul(O::c(0.5f), O::add(O::c(tau0), O::sqrt(arg)));
+  const V om = O::div(O::c(1.0f), tau);
+  const V keep = O::sub(O::c(1.0f), om);
+  const V pre = O::fma(O::c(-0.5f), om, O::c(1.0f));
+  const V uF3 = O::mul(O::c(3.0f), O::fma(ux, m.Fx, O::fma(uy, m.Fy, O::mul(uz, m.Fz))));
+  {
+    const V pw = O::mul(pre, O::c(wgt(0)));
+    emit(0, O::fma(keep, f[0], O::fma(om, O::mul(O::c(wgt(0)), base), O::neg(O::mul(pw, uF3)))));
+  }
+#pragma unroll
+  for (int i = 1; i < NQ; i += 2) {
+    const V e = pair_dot<V>(i, ux, uy, uz);
+    const V h = pair_dot<V>(i, m.Fx, m.Fy, m.Fz);
+    const V sym = O::mul(O::c(wgt(i)), O::fma(O::mul(r45, e), e, base));  // recomputed: fewer live registers
+    const V pw = O::mul(pre, O::c(wgt(i)));
+    const V even = O::fma(om, sym, O::mul(pw, O::fma(O::mul(O::c(9.0f), e), h, O::neg(uF3))));
+    const V odd = O::fma(om, O::mul(O::mul(O::c(wgt(i)), r3), e), O::mul(O::mul(O::c(3.0f), pw), h));
+    emit(i, O::fma(keep, f[i], O::add(even, odd)));
+    emit(i + 1, O::fma(keep, f[i + 1], O::sub(even, odd)));
   }
 }
 
@@ -687,12 +862,17 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
 // a tile and the consumers may leave at the first empty stage with no copy in
 // flight.  (Issuing prologue fills from several warps at once broke this and
 // let a block end with copies still landing in its shared memory.)
-template <int XT, int S, bool STATS, bool VAR>
+// CPT: cells per thread along x, 1 or 2 (16-bit storage, default model:
+// packed FP32x2 arithmetic on two adjacent cells, one 32-bit access per pair
+// where the pair is aligned); the block is (XT / CPT) x (256 CPT / XT).
+template <int XT, int S, bool STATS, bool VAR, int CPT>
 __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part,
                                            bool dynamic) {
+  static_assert(CPT == 1 || (CPT == 2 && !VAR), "two cells per thread: default model only");
   using T = typename Store<S>::T;
   using Gm = Geo<XT, S>;
   using St = Stage<XT, S>;
+  constexpr int TPR = XT / CPT;  // threads per tile row
   extern __shared__ __align__(128) unsigned char smem[];
   // per-thread statistics sums, kept in shared memory rather than registers
   // (the collision needs every register the three-blocks-per-SM budget allows)
@@ -706,8 +886,8 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   __shared__ int4 s_geo[8];           // (xc, zg, y, 1) of the tile each stage holds; y < 0: none
 
   const int tx = threadIdx.x;
-  const int tid = threadIdx.y * XT + tx;
-  const int nthreads = XT * blockDim.y;
+  const int tid = threadIdx.y * TPR + tx;
+  const int nthreads = TPR * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5;
   const unsigned int nwarps = (unsigned int)nthreads / 32;
   const int stage_bytes = (int)blockDim.y * NQ * St::SROW * (int)sizeof(T);
@@ -790,7 +970,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   }
   if (sizeof(T) == 2) __syncthreads();
   const float gx = sizeof(T) == 2 ? s_gx : controlled_gx(p, lane), gy = p.g[1], gz = p.g[2];
-  T* dst = static_cast<T*>(p.dst) + Gm::G + tx;
+  T* dst = static_cast<T*>(p.dst) + Gm::G + CPT * tx;
   T* const dst0 = static_cast<T*>(p.dst) + Gm::G;  // slot G of direction 0, chunk-row 0
 
   // Issue the next fill if its stage has been released by every warp and no
@@ -842,109 +1022,274 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
     }
     const int4 gq = s_geo[st];  // published by the fill (mbarrier release/acquire)
     if (gq.z < 0) break;        // no tile left for this block
-    const int xc = gq.x, y = gq.z;
-    const int x = xc * XT + tx;
-    const int z = gq.y * blockDim.y + threadIdx.y;
-    const bool active = (x < p.nx) && (z < p.nz);
-    if (STATS && (y != stat_y || (flush_on_chunk && xc != stat_xc))) {
-      if (stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
-      stat_y = y;
-      stat_xc = xc;
-    }
+    if constexpr (CPT == 1) {
+      const int xc = gq.x, y = gq.z;
+      const int x = xc * XT + tx;
+      const int z = gq.y * blockDim.y + threadIdx.y;
+      const bool active = (x < p.nx) && (z < p.nz);
+      if (STATS && (y != stat_y || (flush_on_chunk && xc != stat_xc))) {
+        if (stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+        stat_y = y;
+        stat_xc = xc;
+      }
 
-    float f[NQ];
-    Macro m;
-    if (active) {
-      const T* sm = reinterpret_cast<const T*>(stage) + threadIdx.y * NQ * St::SROW + St::H + tx;
-      // streaming from the staged rows; at a free-slip top the staged row is
-      // already the mirrored one, so only bounce-back (own column) and the
-      // equilibrium top (constant) differ, on the five directions entering
-      // through the wall
-#pragma unroll
-      for (int i = 0; i < NQ; i++) f[i] = Store<S>::to_float(sm[i * St::SROW - cx(i)]);
-      if (p.y_walls) {
-        if (y == 0) {
-#pragma unroll
-          for (int i = 0; i < NQ; i++)
-            if (cy(i) == 1) f[i] = Store<S>::to_float(sm[i * St::SROW]);
-        }
-        if (y == p.ny - 1 && p.top != 2) {
-#pragma unroll
-          for (int i = 0; i < NQ; i++)
-            if (cy(i) == -1) f[i] = p.top == 1 ? Store<S>::to_float(sm[i * St::SROW]) : p.feq_top[i];
-        }
-      }
-      if (p.accel0 != nullptr && y == 0) {
-        const float2 a = p.accel0[(long long)z * p.nx + x];
-        m = moments<VAR>(f, gx + a.x, gy, gz + a.y, drag_factor(p, x, y), p.drag_x_only);
-      } else {
-        m = moments<VAR>(f, gx, gy, gz, drag_factor(p, x, y), p.drag_x_only);
-      }
-    }
-    // release the stage: the moments consumed every staged value of this warp
-    __syncwarp();
-    if (lane == 0) atomicAdd(&s_done[st], 1u);
-    if (active) {
-      const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
-      T* out = dst + (long long)(unsigned)(crow0 + xc) * Gm::ROW;
-      // ghost slots this cell feeds (edge lanes only): its c_x = +1 values to
-      // the left ghost of the chunk on its right, its c_x = -1 values to the
-      // right ghost of the chunk on its left (periodic wrap), or beside itself
-      // at an outflow (zero gradient); at an x-halo face none (the halo
-      // exchange sends them to the neighbouring slab and fills these ghosts)
-      T* gr = nullptr;
-      T* gl = nullptr;
-      if (tx == 0 || tx == XT - 1 || x == p.nx - 1) {
-        if (x == p.nx - 1) {
-          if (p.x_io == X_PERIODIC) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
-          else if (p.x_io == X_INOUT) gl = out + 1;  // outflow: its own slot G + n (a one-cell last chunk: below)
-        } else if (tx == XT - 1) {
-          gr = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
-        }
-        if (x == 0) {
-          if (p.x_io == X_PERIODIC) {
-            const int xl = p.nxc - 1;
-            gl = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
+      float f[NQ];
+      Macro m;
+      MacroV<float> mv;
+      if (active) {
+        const T* sm = reinterpret_cast<const T*>(stage) + threadIdx.y * NQ * St::SROW + St::H + tx;
+        // streaming from the staged rows; at a free-slip top the staged row is
+        // already the mirrored one, so only bounce-back (own column) and the
+        // equilibrium top (constant) differ, on the five directions entering
+        // through the wall
+  #pragma unroll
+        for (int i = 0; i < NQ; i++) f[i] = Store<S>::to_float(sm[i * St::SROW - cx(i)]);
+        if (p.y_walls) {
+          if (y == 0) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cy(i) == 1) f[i] = Store<S>::to_float(sm[i * St::SROW]);
           }
-        } else if (tx == 0) {
-          gl = dst0 + (long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT;
+          if (y == p.ny - 1 && p.top != 2) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cy(i) == -1) f[i] = p.top == 1 ? Store<S>::to_float(sm[i * St::SROW]) : p.feq_top[i];
+          }
+        }
+        float gxc = gx, gzc = gz;
+        if (p.accel0 != nullptr && y == 0) {
+          const float2 a = p.accel0[(long long)z * p.nx + x];
+          gxc = gx + a.x;
+          gzc = gz + a.y;
+        }
+        const float kd = drag_factor(p, x, y);
+        if (VAR) {
+          m = moments<VAR>(f, gxc, gy, gzc, kd, p.drag_x_only);
+        } else {
+          mv = moments_v<float>(f, gxc, gy, gzc, kd, kd > 0.f);
+          m = Macro{mv.drho, mv.rho, mv.ux, mv.uy, mv.uz, mv.Fx, mv.Fy, mv.Fz};
         }
       }
-      collide<VAR>(f, m, p.tau0, p.c18, p.edm, p.tau_rho2, [&](int i, float v) {
-        if (kCheckBounds) {
-          const long long set = (long long)p.ny * p.nz * p.nxc * Gm::ROW;
-          T* const d0 = static_cast<T*>(p.dst);
-          if (in_range(out + i * Gm::XTP - d0, 1, set, p.state)) Store<S>::st(out + i * Gm::XTP, v);
-          if (cx(i) == 1 && gr && in_range(gr + i * Gm::XTP - d0, 1, set, p.state))
-            Store<S>::st(gr + i * Gm::XTP, v);
-          if (cx(i) == -1 && gl && in_range(gl + i * Gm::XTP - d0, 1, set, p.state))
-            Store<S>::st(gl + i * Gm::XTP, v);
-          return;
+      // release the stage: the moments consumed every staged value of this warp
+      __syncwarp();
+      if (lane == 0) atomicAdd(&s_done[st], 1u);
+      if (active) {
+        const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
+        T* out = dst + (long long)(unsigned)(crow0 + xc) * Gm::ROW;
+        // ghost slots this cell feeds (edge lanes only): its c_x = +1 values to
+        // the left ghost of the chunk on its right, its c_x = -1 values to the
+        // right ghost of the chunk on its left (periodic wrap), or beside itself
+        // at an outflow (zero gradient); at an x-halo face none (the halo
+        // exchange sends them to the neighbouring slab and fills these ghosts)
+        T* gr = nullptr;
+        T* gl = nullptr;
+        if (tx == 0 || tx == XT - 1 || x == p.nx - 1) {
+          if (x == p.nx - 1) {
+            if (p.x_io == X_PERIODIC) gr = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
+            else if (p.x_io == X_INOUT) gl = out + 1;  // outflow: its own slot G + n (a one-cell last chunk: below)
+          } else if (tx == XT - 1) {
+            gr = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
+          }
+          if (x == 0) {
+            if (p.x_io == X_PERIODIC) {
+              const int xl = p.nxc - 1;
+              gl = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
+            }
+          } else if (tx == 0) {
+            gl = dst0 + (long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT;
+          }
         }
-        Store<S>::st(out + i * Gm::XTP, v);
-        if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
-        if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
-      });
-      if (p.io_one && x == p.nx - 1) {
-        // a one-cell last chunk at an outflow: gl went to the previous
-        // chunk's right ghost, so the zero-gradient copy beside the cell is
-        // taken from the line it just stored
+        auto put = [&](int i, float v) {
+          if (kCheckBounds) {
+            const long long set = (long long)p.ny * p.nz * p.nxc * Gm::ROW;
+            T* const d0 = static_cast<T*>(p.dst);
+            if (in_range(out + i * Gm::XTP - d0, 1, set, p.state)) Store<S>::st(out + i * Gm::XTP, v);
+            if (cx(i) == 1 && gr && in_range(gr + i * Gm::XTP - d0, 1, set, p.state))
+              Store<S>::st(gr + i * Gm::XTP, v);
+            if (cx(i) == -1 && gl && in_range(gl + i * Gm::XTP - d0, 1, set, p.state))
+              Store<S>::st(gl + i * Gm::XTP, v);
+            return;
+          }
+          Store<S>::st(out + i * Gm::XTP, v);
+          if (cx(i) == 1 && gr) Store<S>::st(gr + i * Gm::XTP, v);
+          if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
+        };
+        if (VAR) collide<VAR>(f, m, p.tau0, p.c18, p.edm, p.tau_rho2, put);
+        else collide_v<float>(f, mv, p.tau0, p.c18, put);
+        if (p.io_one && x == p.nx - 1) {
+          // a one-cell last chunk at an outflow: gl went to the previous
+          // chunk's right ghost, so the zero-gradient copy beside the cell is
+          // taken from the line it just stored
+  #pragma unroll
+          for (int i = 0; i < NQ; i++)
+            if (cx(i) == -1 &&
+                (!kCheckBounds || in_range(out + 1 + i * Gm::XTP - static_cast<T*>(p.dst), 1,
+                                           (long long)p.ny * p.nz * p.nxc * Gm::ROW, p.state)))
+              out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
+        }
+        ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
+        // health: a non-finite density (a non-finite velocity or population
+        // makes the density non-finite by the next step at the latest)
+        bad |= !(fabsf(m.drho) < 1e30f);
+        if (STATS) {
+          qs[0 * 256] += m.ux; qs[1 * 256] += m.uy; qs[2 * 256] += m.uz;
+          qs[3 * 256] += m.ux * m.ux; qs[4 * 256] += m.uy * m.uy; qs[5 * 256] += m.uz * m.uz;
+          qs[6 * 256] += m.ux * m.uy; qs[7 * 256] += m.ux * m.uz; qs[8 * 256] += m.uy * m.uz;
+          last_x = x;
+        }
+      }
+    } else {
+      const int xc = gq.x, y = gq.z;
+      const int x = xc * XT + 2 * tx;  // cells x and x + 1
+      const int z = gq.y * blockDim.y + threadIdx.y;
+      const bool active = (x < p.nx) && (z < p.nz);
+      const bool act1 = active && x + 1 < p.nx;
+      if (STATS && (y != stat_y || (flush_on_chunk && xc != stat_xc))) {
+        if (stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+        stat_y = y;
+        stat_xc = xc;
+      }
+
+      float2 f[NQ];
+      MacroV<float2> m;
+      if (active) {
+        const T* sm = reinterpret_cast<const T*>(stage) + threadIdx.y * NQ * St::SROW + St::H + 2 * tx;
+        // streaming from the staged rows: rows with c_x = 0 hold the pair at an
+        // aligned offset (one 32-bit load), the others one cell to the side
+  #pragma unroll
+        for (int i = 0; i < NQ; i++) {
+          if (cx(i) == 0) {
+            f[i] = Store<S>::ld2(sm + i * St::SROW);
+          } else {
+            f[i].x = Store<S>::to_float(sm[i * St::SROW - cx(i)]);
+            f[i].y = Store<S>::to_float(sm[i * St::SROW + 1 - cx(i)]);
+          }
+        }
+        if (p.y_walls) {
+          if (y == 0) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cy(i) == 1) f[i] = Store<S>::ld2(sm + i * St::SROW);
+          }
+          if (y == p.ny - 1 && p.top != 2) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cy(i) == -1)
+                f[i] = p.top == 1 ? Store<S>::ld2(sm + i * St::SROW) : make_float2(p.feq_top[i], p.feq_top[i]);
+          }
+        }
+        float2 gxc = make_float2(gx, gx), gzc = make_float2(gz, gz);
+        if (p.accel0 != nullptr && y == 0) {
+          const float2* a = p.accel0 + (long long)z * p.nx + x;
+          const float2 a0 = a[0], a1 = act1 ? a[1] : make_float2(0.f, 0.f);
+          gxc = make_float2(gx + a0.x, gx + a1.x);
+          gzc = make_float2(gz + a0.y, gz + a1.y);
+        }
+        const float2 kd = make_float2(drag_factor(p, x, y), drag_factor(p, x + 1, y));
+        m = moments_v<float2>(f, gxc, make_float2(gy, gy), gzc, kd, kd.x > 0.f || kd.y > 0.f);
+      }
+      // release the stage: the moments consumed every staged value of this warp
+      __syncwarp();
+      if (lane == 0) atomicAdd(&s_done[st], 1u);
+      if (active) {
+        const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
+        T* out = dst + (long long)(unsigned)(crow0 + xc) * Gm::ROW;
+        const long long set = (long long)p.ny * p.nz * p.nxc * Gm::ROW;
+        T* const d0 = static_cast<T*>(p.dst);
+        auto put1 = [&](T* q, float v) {
+          if (!kCheckBounds || in_range(q - d0, 1, set, p.state)) Store<S>::st(q, v);
+        };
+        ub_fix += __float2ll_rn(m.ux.x * 4294967296.0f);
+        bad |= !(fabsf(m.drho.x) < 1e30f);
+        if (act1) {
+          ub_fix += __float2ll_rn(m.ux.y * 4294967296.0f);
+          bad |= !(fabsf(m.drho.y) < 1e30f);
+        }
+        if (STATS) {
+          const float2 u = m.ux, v = m.uy, w = m.uz;
+          const bool split = act1 && p.nbins > 1 &&
+                             ((long long)x * p.nbins) / p.nx != ((long long)(x + 1) * p.nbins) / p.nx;
+          if (act1 && !split) {  // both cells in the thread's sums
+            qs[0 * 256] += u.x + u.y; qs[1 * 256] += v.x + v.y; qs[2 * 256] += w.x + w.y;
+            qs[3 * 256] += u.x * u.x + u.y * u.y; qs[4 * 256] += v.x * v.x + v.y * v.y;
+            qs[5 * 256] += w.x * w.x + w.y * w.y; qs[6 * 256] += u.x * v.x + u.y * v.y;
+            qs[7 * 256] += u.x * w.x + u.y * w.y; qs[8 * 256] += v.x * w.x + v.y * w.y;
+          } else {
+            qs[0 * 256] += u.x; qs[1 * 256] += v.x; qs[2 * 256] += w.x;
+            qs[3 * 256] += u.x * u.x; qs[4 * 256] += v.x * v.x; qs[5 * 256] += w.x * w.x;
+            qs[6 * 256] += u.x * v.x; qs[7 * 256] += u.x * w.x; qs[8 * 256] += v.x * w.x;
+            if (split) {
+              // the pair straddles an x-bin edge: the second cell's sums go straight out
+              const long long mm = (long long)p.nbins * p.ny;
+              double* acc = p.stats + ((long long)(x + 1) * p.nbins) / p.nx * p.ny + y;
+              atomicAdd(acc + 0 * mm, (double)u.y); atomicAdd(acc + 1 * mm, (double)v.y);
+              atomicAdd(acc + 2 * mm, (double)w.y); atomicAdd(acc + 3 * mm, (double)(u.y * u.y));
+              atomicAdd(acc + 4 * mm, (double)(v.y * v.y)); atomicAdd(acc + 5 * mm, (double)(w.y * w.y));
+              atomicAdd(acc + 6 * mm, (double)(u.y * v.y)); atomicAdd(acc + 7 * mm, (double)(u.y * w.y));
+              atomicAdd(acc + 8 * mm, (double)(v.y * w.y));
+            }
+          }
+          last_x = x;
+        }
+        collide_v<float2>(f, m, p.tau0, p.c18, [&](int i, float2 v) {
+          T* o = out + i * Gm::XTP;
+          if (act1) {
+            if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
+          } else {
+            put1(o, v.x);
+          }
+        });
+        // ghost slots the two cells feed (as for one cell per thread: cell x can
+        // be the first of its chunk or the last of the domain, cell x + 1 the
+        // last of its chunk or of the domain), copied from the line just
+        // stored (edge lanes only; the pointers are not live in the collision)
+        T* gr0 = nullptr;
+        T* gl0 = nullptr;
+        T* gr1 = nullptr;
+        T* gl1 = nullptr;
+        if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
+          if (x == p.nx - 1) {
+            if (p.x_io == X_PERIODIC) gr0 = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
+            else if (p.x_io == X_INOUT) gl0 = out + 1;
+          }
+          if (act1 && x + 1 == p.nx - 1) {
+            if (p.x_io == X_PERIODIC) gr1 = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
+            else if (p.x_io == X_INOUT) gl1 = out + 2;
+          } else if (act1 && tx == TPR - 1) {
+            gr1 = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
+          }
+          if (x == 0) {
+            if (p.x_io == X_PERIODIC) {
+              const int xl = p.nxc - 1;
+              gl0 = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
+            }
+          } else if (tx == 0) {
+            gl0 = dst0 + (long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT;
+          }
+        }
+        if (gr0 || gl0 || gr1 || gl1) {
 #pragma unroll
-        for (int i = 0; i < NQ; i++)
-          if (cx(i) == -1 &&
-              (!kCheckBounds || in_range(out + 1 + i * Gm::XTP - static_cast<T*>(p.dst), 1,
-                                         (long long)p.ny * p.nz * p.nxc * Gm::ROW, p.state)))
-            out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
-      }
-      ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
-      // health: a non-finite density (a non-finite velocity or population
-      // makes the density non-finite by the next step at the latest)
-      bad |= !(fabsf(m.drho) < 1e30f);
-      if (STATS) {
-        qs[0 * 256] += m.ux; qs[1 * 256] += m.uy; qs[2 * 256] += m.uz;
-        qs[3 * 256] += m.ux * m.ux; qs[4 * 256] += m.uy * m.uy; qs[5 * 256] += m.uz * m.uz;
-        qs[6 * 256] += m.ux * m.uy; qs[7 * 256] += m.ux * m.uz; qs[8 * 256] += m.uy * m.uz;
-        last_x = x;
+          for (int i = 0; i < NQ; i++) {
+            const T* o = out + i * Gm::XTP;
+            if (cx(i) == 1) {
+              if (gr0) put1(gr0 + i * Gm::XTP, Store<S>::to_float(__ldcg(o)));
+              if (gr1) put1(gr1 + i * Gm::XTP, Store<S>::to_float(__ldcg(o + 1)));
+            }
+            if (cx(i) == -1) {
+              if (gl0) put1(gl0 + i * Gm::XTP, Store<S>::to_float(__ldcg(o)));
+              if (gl1) put1(gl1 + i * Gm::XTP, Store<S>::to_float(__ldcg(o + 1)));
+            }
+          }
+        }
+        if (p.io_one && x == p.nx - 1) {
+          // a one-cell last chunk at an outflow (its cell is the pair's first):
+          // the zero-gradient copy beside the cell from the line it just stored
+  #pragma unroll
+          for (int i = 0; i < NQ; i++)
+            if (cx(i) == -1 &&
+                (!kCheckBounds || in_range(out + 1 + i * Gm::XTP - d0, 1, set, p.state)))
+              out[1 + i * Gm::XTP] = __ldcg(out + i * Gm::XTP);
+        }
       }
     }
   }
@@ -970,10 +1315,10 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 // One domain: block b walks its static run of tiles, then shares the rest.
 // VAR: the model-variant form (flags in p); the default form has none of
 // their code.
-template <int XT, int S, bool STATS, bool VAR>
-__global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
-  step_tiles<XT, S, STATS, VAR>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
-                                blockIdx.x, true);
+template <int XT, int S, bool STATS, bool VAR, int CPT>
+__global__ void __launch_bounds__(256, CPT == 1 ? 3 : 2) step_kernel(StepParams p) {
+  step_tiles<XT, S, STATS, VAR, CPT>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
+                                     blockIdx.x, true);
 }
 
 // Many independent domains (an ensemble of boxes) in one launch: work item
@@ -984,9 +1329,9 @@ struct BatchWork {
   long long t0;
 };
 
-template <int XT, int S, bool STATS>
-__global__ void __launch_bounds__(256, 3) batch_step_kernel(const StepParams* __restrict__ boxes,
-                                                            const BatchWork* __restrict__ work) {
+template <int XT, int S, bool STATS, int CPT>
+__global__ void __launch_bounds__(256, CPT == 1 ? 3 : 2) batch_step_kernel(
+    const StepParams* __restrict__ boxes, const BatchWork* __restrict__ work) {
   __shared__ __align__(16) StepParams s_p;
   const BatchWork w = work[blockIdx.x];
   {
@@ -998,7 +1343,7 @@ __global__ void __launch_bounds__(256, 3) batch_step_kernel(const StepParams* __
       dst[k] = src[k];
   }
   __syncthreads();
-  step_tiles<XT, S, STATS, false>(s_p, w.t0, w.ntile, -1, false);
+  step_tiles<XT, S, STATS, false, CPT>(s_p, w.t0, w.ntile, -1, false);
 }
 
 // ---- ghost slots from the cells (after init, set_f) ----------------------------------

@@ -10,16 +10,21 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm_aa.cuh"
 #include "lbm_features.cuh"
 
 namespace lbm {
 
 template <int XT, int S>
 struct Kern {
-  // Largest dynamic shared memory every step kernel may use (stage ring).
-  static void configure(size_t stage_smem);
-  // Resident blocks per SM of the step kernels (the smaller over their forms).
-  static int occupancy(dim3 block, size_t smem);
+  // Largest dynamic shared memory the step kernels may use (stage ring) in
+  // the default and in the variant form.
+  static void configure(size_t smem_default, size_t smem_variant);
+  // Cells per thread along x of the step kernel of that form (1 or 2); its
+  // block is (XT / cpt) x (256 cpt / XT) threads.
+  static int cells_per_thread(bool variant);
+  // Resident blocks per SM of the step kernels of that form.
+  static int occupancy(dim3 block, size_t smem, bool variant);
   // One time step (programmatic dependent launch when pdl).  variant: the
   // model-variant form (streamwise-only drag, exact-difference forcing,
   // tau_total with 1/rho^2), selected by the flags in p.
@@ -40,6 +45,18 @@ struct Kern {
                         void* hi);
   static void halo_unpack(int blocks, cudaStream_t s, const StepParams& p, void* f, const void* lo,
                           const void* hi);
+};
+
+// AA-pattern storage (lbm_aa.cuh), per storage type (no chunk width).
+template <int S>
+struct KernAA {
+  static int occupancy();  // resident blocks per SM of the step kernel (256 threads)
+  static void fill(int blocks, cudaStream_t s, const StepParams& p);
+  static void step(int blocks, cudaStream_t s, const AAStep& a, bool stats, bool variant);
+  static void init(int blocks, cudaStream_t s, const StepParams& p, const InitParams& ip);
+  static void mass(int blocks, cudaStream_t s, const StepParams& p, double* partial);
+  static void macro(int blocks, cudaStream_t s, const StepParams& p, float* out);
+  static void macro_d(int blocks, cudaStream_t s, const StepParams& p, double* out);
 };
 
 // ---- the learned correction's network (lbm_mlp.cu; kernels in lbm_mlp.cuh) ----
@@ -65,6 +82,9 @@ void mlp_launch_adam(int blocks, cudaStream_t s, float* th, const float* g, floa
 LBM_DECLARE_KERN(0)
 LBM_DECLARE_KERN(1)
 LBM_DECLARE_KERN(2)
+extern template struct KernAA<0>;
+extern template struct KernAA<1>;
+extern template struct KernAA<2>;
 #undef LBM_DECLARE_KERN
 
 }  // namespace lbm

@@ -128,6 +128,20 @@ def test_model_variants_and_halo_checked_without_a_device():
         assert P.lbm_batch_workspace_bytes(arr, P.LBM_F16_SHIFTED, 1) == 0, kw
 
 
+def test_aa_storage_argument_without_a_device():
+    g = _grid()
+    aa = P.LBM_STORAGE_AA
+    pull = P.lbm_workspace_bytes(g, P.LBM_F32, 1)
+    one = P.lbm_workspace_bytes(g, P.LBM_F32 | aa, 1)
+    # one set with a one-cell ghost layer: (64 + 2 -> 96) x 34 x 18 cells, 19 directions
+    assert 19 * 96 * 34 * 18 * 4 <= one < pull
+    assert P.lbm_workspace_bytes(g, P.LBM_F16_SHIFTED | aa, 1) < one
+    assert P.lbm_workspace_bytes(g, 0x200, 1) == 0          # unknown flag
+    assert P.lbm_workspace_bytes(g, 3 | aa, 1) == 0         # unknown type
+    halo = _grid(bc=(P.LBM_BC_HALO, P.LBM_BC_HALO, 1, 2, 0, 0))
+    assert P.lbm_workspace_bytes(halo, P.LBM_F32 | aa, 1) == 0  # slabs use two sets
+
+
 def test_null_context_calls_fail_cleanly():
     L = P.lib()
     assert L.lbm_step(None, 1) == P.LBM_ERR_ARG

@@ -1,8 +1,9 @@
 """The checked build (LBM_CHECK_BOUNDS: every bulk copy and global store of
-the step verified against its buffer) on every small boundary combination,
-ragged rows, chunked rows, a one-cell outflow chunk, 16-bit storage, an
-ensemble and x-binned statistics: no index leaves its buffer and the results
-still match the FP64 oracle.  Runs in a child process, which loads the checked
+the step, and every access of the AA-pattern kernels, verified against its
+buffer) on every small boundary combination, ragged rows, chunked rows, a
+one-cell outflow chunk, 16-bit storage, an ensemble, x-binned statistics, the
+model variants, halo slabs and AA-pattern storage: no index leaves its buffer
+and the results still match the FP64 oracle.  Runs in a child process, which loads the checked
 library instead of the default one."""
 import os
 import subprocess
@@ -66,6 +67,19 @@ for c in (cases[2].replace(drag_streamwise_only=1, forcing_scheme=1, sgs_rho_pow
     err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     assert err <= 1e-6, (c.name, "variant", err)
     d.close()
+# AA-pattern storage: every load and store of the fill and step kernels checked
+for c in cases:
+    for st in (P.LBM_F32 | P.LBM_STORAGE_AA, P.LBM_F16_SHIFTED | P.LBM_STORAGE_AA):
+        d, o = P.Domain(c, st), oracle.Oracle(c)
+        d.stats_reset(True)
+        d.step(11)
+        o.step(11)
+        d.stats()
+        a, b = d.get_f(), o.get_f()
+        err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        assert err <= (1e-6 if st == P.LBM_F32 | P.LBM_STORAGE_AA else 5e-3), (c.name, "AA", st, err)
+        d.close()
+        o.close()
 from paper_2206_15454_b300 import slabs as S
 c = W.channel_les(150, 9, 6).replace(u_bulk_target=0.0, ctrl_gain=0.0)
 whole = P.Domain(c)
