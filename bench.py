@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--storage", choices=["f32", "f16s", "bf16s"], default="f32")
+    ap.add_argument("--storage", choices=["f32", "f16s", "bf16s", "f32-aa", "f16s-aa", "bf16s-aa"],
+                    default="f32")
     ap.add_argument("--no-half", action="store_true", help="skip the FP16/BF16 storage legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-box ensemble leg")
@@ -79,10 +80,12 @@ def kernel_source_hash(text=None):
     return hashlib.sha256(b"lbm_device.cuh" + code_tokens(text).encode()).hexdigest()[:16]
 
 
-def measured_traffic(storage_name, cells, workload="channel"):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary
-    (the channel captures, or the canopy one), scaled from the captured case to
-    `cells`; None if the kernel changed since."""
+def measured_traffic_rw(storage_name, cells, workload="channel"):
+    """(read, write) DRAM bytes per launch of the step kernel from the committed
+    ncu summary (the channel captures, or the canopy one), scaled from the
+    captured case to `cells`; None if the kernel changed since.  The write
+    count of a single captured launch misses what is still in L2 when the
+    kernel ends, so read and write are reported apart."""
     try:
         with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as fh:
             t = json.load(fh)
@@ -93,7 +96,13 @@ def measured_traffic(storage_name, cells, workload="channel"):
     e = (t.get("storage", {}) if workload == "channel" else t.get(workload, {})).get(storage_name)
     if not e:
         return None
-    return (e["dram_read_bytes"] + e["dram_write_bytes"]) * cells / e["cells"]
+    return e["dram_read_bytes"] * cells / e["cells"], e["dram_write_bytes"] * cells / e["cells"]
+
+
+def measured_traffic(storage_name, cells, workload="channel"):
+    """Read plus write DRAM bytes per launch (see measured_traffic_rw), or None."""
+    rw = measured_traffic_rw(storage_name, cells, workload)
+    return None if rw is None else rw[0] + rw[1]
 
 
 def peaks():
@@ -192,9 +201,15 @@ def max_over_ranks(ws, v):
 
 # ---------------------------------------------------------------------- our arm ---
 
-def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
+def time_storage(P, W, storage, steps, warmup, ws, with_stats=True, soak_s=0.0):
+    """The channel in one storage: `warmup` steps, the timed region of `steps`
+    launches, single launches between events, four more timed regions, then
+    (soak_s > 0) more steps of the same loop until soak_s seconds have passed
+    since the warm-up began, so a clock sampler running around this call sees
+    the kernel's load for at least that long."""
     import torch
 
+    t_start = time.perf_counter()
     case = W.channel_les()
     d = P.Domain(case, storage)
     d.mass0 = d.mass()  # FP64 global mass of the initial state (mass drift below)
@@ -236,6 +251,9 @@ def time_storage(P, W, storage, steps, warmup, ws, with_stats=True):
         repeats.append(t_begin.elapsed_time(t_end))
     d.sync()
     d.repeats_ms = repeats
+    while time.perf_counter() - t_start < soak_s:
+        d.step(200)
+        d.sync()
     return d, case, total_ms, per_launch_ms
 
 
@@ -405,6 +423,113 @@ def cpu_baseline(case_factory, seconds):
             f" channel (FP64, OpenMP over z planes, {threads} threads)"}
 
 
+CANOPY_ERR = dict(nx=128, ny=32, nz=32, h=8.0, canopy_x0=32, xbin=32)
+CANOPY_ERR_STEPS = (1000, 2000)  # spin-up, statistics window
+
+
+def cpu_baseline_leg(W):
+    """The FP64 oracle as it stands, on this host's cores, on two bounded
+    samples: 100 full time steps of the 256x128x128 channel (the reported
+    MLUPS) and a statistics run of a 128x32x32 canopy boundary layer
+    (1000 + 2000 steps).  Returns (the baseline record, the oracle's end states,
+    which the GPU results state their errors against)."""
+    import oracle
+
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    case = W.channel_les()
+    o = oracle.Oracle(case)
+    t0 = time.perf_counter()
+    o.step(100)
+    dt = time.perf_counter() - t0
+    f_channel = o.get_f()
+    o.close()
+    cc = W.canopy_abl(**CANOPY_ERR)
+    oc = oracle.Oracle(cc)
+    spin, window = CANOPY_ERR_STEPS
+    t1 = time.perf_counter()
+    oc.step(spin)
+    oc.stats_reset(True)
+    oc.step(window)
+    dt2 = time.perf_counter() - t1
+    s_canopy = oc.stats()[0]
+    oc.close()
+    rec = {"value": round(case.cells * 100 / dt / 1e6, 2), "unit": "MLUPS", "cores": threads,
+           "kind": "oracle",
+           "sample": f"100 full time steps of the 256x128x128 channel (FP64, OpenMP over z "
+                     f"planes, {threads} threads, {dt:.1f} s)",
+           "canopy_sample": {"value": round(cc.cells * (spin + window) / dt2 / 1e6, 2),
+                             "unit": "MLUPS",
+                             "sample": f"{spin} + {window} steps of a 128x32x32 canopy boundary "
+                                       f"layer with statistics ({dt2:.1f} s)"}}
+    return rec, {"channel_f_100": f_channel, "canopy_stats": s_canopy}
+
+
+def population_error(P, W, storage, ref):
+    """Populations after 100 steps of the channel against the FP64 oracle's:
+    relative L2 and the largest single error over max |f - w|."""
+    import numpy as np
+
+    d = P.Domain(W.channel_les(), storage)
+    d.step(100)
+    f = d.get_f()
+    d.close()
+    fo = ref["channel_f_100"]
+    w = np.array([1.0 / 3.0] + [1.0 / 18.0] * 6 + [1.0 / 36.0] * 12)[:, None, None, None]
+    num = den = elem = scale = 0.0
+    for q in range(19):
+        e = f[q] - fo[q]
+        num += float(np.sum(e * e))
+        den += float(np.sum(fo[q] * fo[q]))
+        elem = max(elem, float(np.abs(e).max()))
+        scale = max(scale, float(np.abs(fo[q] - w[q]).max()))
+    return {"rel_l2_f_after_100_steps": float(np.sqrt(num / den)),
+            "max_element_error_over_max_f_minus_w": elem / scale,
+            "case": "channel 256x128x128, 100 steps, same seed"}
+
+
+def canopy_profile_errors(P, ref):
+    """Mean-velocity and <u'v'> profiles (per x-bin) of the canopy sample on the
+    GPU in each storage against the FP64 oracle's: largest deviation over the
+    profiles relative to the largest magnitude."""
+    import numpy as np
+    import workloads as W
+
+    so = ref["canopy_stats"]
+    out = {"case": "canopy 128x32x32 (h=8, inflow/outflow, x-bins of 32), "
+                   f"{CANOPY_ERR_STEPS[0]} + {CANOPY_ERR_STEPS[1]} steps"}
+    for name in ("f32", "f16s", "bf16s"):
+        d = P.Domain(W.canopy_abl(**CANOPY_ERR), P.STORAGE_NAMES[name])
+        d.step(CANOPY_ERR_STEPS[0])
+        d.stats_reset(True)
+        d.step(CANOPY_ERR_STEPS[1])
+        s, _ = d.stats()
+        d.close()
+        out[name] = {"mean_u": float(np.abs(s[0] - so[0]).max() / np.abs(so[0]).max()),
+                     "uv": float(np.abs(s[6] - so[6]).max() / np.abs(so[6]).max())}
+    return out
+
+
+def time_aa(P, W, steps, warmup, hbm, ws):
+    """The channel with AA-pattern in-place storage (one population set) in
+    FP32 and FP16: MLUPS, roofline fraction and the workspace beside the
+    two-set pull layout."""
+    out = {"workload": "the same channel, AA-pattern in-place storage"}
+    g = P._case_inputs(W.channel_les())[0]
+    for name in ("f32", "f16s"):
+        st = P.STORAGE_NAMES[name + "-aa"]
+        d, case, tot, _ = time_storage(P, W, st, steps, warmup, ws)
+        d.close()
+        tot = max_over_ranks(ws, tot)
+        ach = P.BYTES_PER_LUP[st] * case.cells / (tot / steps * 1e-3) / 1e9
+        out[name] = {"value": round(case.cells * steps * ws / (tot * 1e-3) / 1e6, 1),
+                     "unit": "MLUPS", "ms_per_step": tot / steps,
+                     "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                                  "unit": "GB/s", "frac": round(ach / hbm, 4)},
+                     "workspace_bytes": P.lbm_workspace_bytes(g, st, 1),
+                     "workspace_bytes_pull": P.lbm_workspace_bytes(g, P.STORAGE_NAMES[name], 1)}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -417,8 +542,12 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     clocks = Clocks(local)
     clocks.start()
-    d, case, total_ms, launch_ms = time_storage(P, W, storage, args.steps, args.warmup, ws)
+    d, case, total_ms, launch_ms = time_storage(P, W, storage, args.steps, args.warmup, ws,
+                                                soak_s=1.5)
     clk = clocks.stop()
+    if clk:
+        clk["window"] = ("nvidia-smi every 50 ms from the start of the warm-up through the timed "
+                         "regions and further steps of the same loop to 1.5 s")
     total_ms = max_over_ranks(ws, total_ms)
     cells = case.cells
     bpl = P.BYTES_PER_LUP[storage]
@@ -432,7 +561,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f32": "f32", "f16s": "f16-storage/f32-compute",
-                  "bf16s": "bf16-storage/f32-compute"}[args.storage],
+                  "bf16s": "bf16-storage/f32-compute"}[args.storage.split("-")[0]],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": cells, "storage": args.storage,
                    "bytes_per_lup": bpl, "l2": "inputs larger than L2 (no flush needed)",
@@ -440,6 +569,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4),
                      "traffic": measured_traffic(args.storage, cells),
+                     "traffic_read_write": measured_traffic_rw(args.storage, cells),
                      "kernel": "step_kernel", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bpl * cells,
                      "launch_ms": step_ms,
@@ -461,23 +591,26 @@ def run_ours(args):
     res["mass"] = {"initial": d.mass0, "after_steps": d.steps_done(), "final": m1,
                    "rel_drift": (m1 - d.mass0) / d.mass0}
     # end to end through the public API with host-side results every step
-    e2e_steps = min(args.steps, 500)
+    e2e_steps = max(1000, min(args.steps, 2000))  # a floor of its own
     dt, d2h = e2e_run(P, d, e2e_steps)
     res["e2e"] = {"value": round(cells * e2e_steps * ws / dt / 1e6, 1), "unit": "MLUPS",
                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                   "note": "per step: lbm_step, lbm_stats_begin (copy of the plane statistics and "
                           "health flags to pinned host memory), lbm_stats_end of the previous "
                           "step's read-out; the flow state stays resident, so a step has no "
-                          "host input"}
+                          "host input (no copy is declared for the input)",
+                  "steps": e2e_steps}
     d.close()
-    # half-precision storage legs (stated error against the FP32 run on the GPU)
+    # the CPU baseline (rank 0): the FP64 oracle as it stands, timed on bounded
+    # samples of the channel and of a small canopy domain; its end states are
+    # also what the GPU results state their errors against
+    ref = None
+    if rank == 0 and not args.no_cpu:
+        res["cpu_baseline"], ref = cpu_baseline_leg(W)
+        res["cpu_baseline"]["single_thread"] = cpu_baseline_single_thread(args.cpu_seconds / 3)
+        res["error_vs_fp64_oracle"] = {"f32": population_error(P, W, P.LBM_F32, ref)}
+    # half-precision storage legs
     if not args.no_half:
-        import numpy as np
-
-        ref = P.Domain(W.channel_les(), P.LBM_F32)
-        ref.step(100)
-        fref = ref.get_f()
-        ref.close()
         for name in ("f16s", "bf16s"):
             st = P.STORAGE_NAMES[name]
             dh, _, tot, lms = time_storage(P, W, st, args.steps, args.warmup, ws)
@@ -486,25 +619,25 @@ def run_ours(args):
             dh.close()
             tot = max_over_ranks(ws, tot)
             ach = P.BYTES_PER_LUP[st] * cells / (tot / args.steps * 1e-3) / 1e9
-            chk = P.Domain(W.channel_les(), st)
-            chk.step(100)
-            err = float(np.linalg.norm(chk.get_f() - fref) / np.linalg.norm(fref))
-            chk.close()
             res[name] = {"value": round(cells * args.steps * ws / (tot * 1e-3) / 1e6, 1),
                          "unit": "MLUPS", "ms_per_step": tot / args.steps,
                          "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
                                       "unit": "GB/s", "frac": round(ach / hbm, 4),
-                                      "traffic": measured_traffic(name, cells)},
-                         "rel_l2_f_vs_f32_after_100_steps": err, "mass": drift}
+                                      "traffic": measured_traffic(name, cells),
+                                      "traffic_read_write": measured_traffic_rw(name, cells)},
+                         "mass": drift}
+            if ref is not None:
+                res[name]["error_vs_fp64_oracle"] = population_error(P, W, st, ref)
+    # AA-pattern in-place storage (one population set) beside the two-set pull scheme
+    res["aa"] = time_aa(P, W, args.steps, args.warmup, hbm, ws)
     if not args.no_canopy:
         res["canopy"] = time_canopy(P, W, min(args.steps, 500), max(args.warmup, 3), hbm)
     if not args.no_ensemble:
         res["ensemble"] = time_ensemble(P, W, min(args.steps, 1000), max(args.warmup, 3), hbm)
     if not args.no_learned:
         res["learned"] = time_learned(P, W, min(args.steps, 100), max(min(args.warmup, 10), 3))
-    if rank == 0 and not args.no_cpu:
-        res["cpu_baseline"] = cpu_baseline(W.channel_les, args.cpu_seconds)
-        res["cpu_baseline"]["single_thread"] = cpu_baseline_single_thread(args.cpu_seconds / 3)
+    if ref is not None and not args.no_canopy:
+        res["canopy"]["profile_error_vs_fp64_oracle"] = canopy_profile_errors(P, ref)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:
@@ -530,10 +663,10 @@ def run_reference(args):
     # about two minutes
     nz_min = min(128, max(8, threads))
     probe = oracle.Oracle(W.channel_les(256, 128, nz_min))
-    probe.step(1)  # first touch
+    probe.step(2)  # first touch
     t0 = time.perf_counter()
-    probe.step(2)
-    per_cell = (time.perf_counter() - t0) / (2 * 256 * 128 * nz_min)
+    probe.step(6)  # steady steps
+    per_cell = (time.perf_counter() - t0) / (6 * 256 * 128 * nz_min)
     probe.close()
     budget = 120.0 / max(1, args.steps + args.warmup)
     nz = int(max(nz_min, min(128, budget / (per_cell * 256 * 128))))
