@@ -15,8 +15,10 @@
 // kernel writes exactly the slots whose upstream cell x - c_i lies outside the
 // domain (ghost slots before B, the cell's own slots before A) with the value
 // the pull scheme's streaming gives (row_source / source_x: periodic wrap,
-// bounce-back, free slip, equilibrium top, inflow, outflow).  The collision is
-// the pull kernel's (moments / collide).
+// bounce-back, free slip, equilibrium top, inflow, outflow).  (Reading those
+// values in place inside the step was tried: the boundary cells' dependent
+// loads made their rows, which a static split gives to few blocks, set the
+// step's duration.)  The collision is the pull kernel's (moments_v / collide_v).
 #pragma once
 
 #include "lbm_device.cuh"
@@ -53,55 +55,75 @@ __device__ __forceinline__ float aa_pull(const StepParams& p, int i, int x, int 
   if (kind == SRC_CONST) return p.feq_top[i];
   if (kind == SRC_OWN_X) return aa_post<S>(p, q, x, ys, zs);
   const int xs = source_x(p, x, cx(i));
-  if (xs < 0) return p.feq_in[ys * NQ + q];
+  // the inflow equilibrium as the pull scheme's inflow ghost slot holds it:
+  // rounded to the storage type
+  if (xs < 0) return Store<S>::to_float(Store<S>::from_double((double)p.feq_in[ys * NQ + q]));
   return aa_post<S>(p, q, xs, ys, zs);
 }
 
-// Boundary fill before a step: for every face cell X and direction i whose
-// upstream cell X - c_i lies outside, the value aa_pull gives goes to the
-// slot the next step reads it from: ghost slot opp(i) at X - c_i before B,
-// slot i at X before A.  Face cells are enumerated per face (edge and corner
-// cells more than once, writing the same value).  Reads touch only slots
-// whose upstream cell is inside, which no fill writes.
+// The five directions entering through a face: face 0/1: x = 0 / nx - 1
+// (c_x = +1 / -1), 2/3: y = 0 / ny - 1, 4/5: z = 0 / nz - 1; d = 0..4.
+__device__ __forceinline__ int aa_inward(int face, int d) {
+  const int axis = face >> 1, sign = (face & 1) ? -1 : 1;
+  int n = 0;
+#pragma unroll
+  for (int i = 1; i < NQ; i++) {
+    const int c = axis == 0 ? cx(i) : axis == 1 ? cy(i) : cz(i);
+    if (c == sign) {
+      if (n == d) return i;
+      n++;
+    }
+  }
+  return 0;
+}
+
+// Boundary fill before a step: for every cell X of the domain's faces and
+// every direction i entering through that face (its upstream cell X - c_i
+// lies outside), aa_pull's value goes to the slot the step reads it from:
+// ghost slot opp(i) at X - c_i before B, slot i at X before A.  Stored, the
+// inflow value is rounded to the storage type as in the pull scheme's ghost
+// slot.  One thread per (face cell, direction), so the loads of the fill are
+// all in flight at once; a cell on an edge or corner is reached through
+// several faces and writes the same value each time.  The fill reads only
+// slots whose upstream cell is inside, which no fill writes.
 template <int S>
 __global__ void aa_fill_kernel(StepParams p) {
   using T = typename Store<S>::T;
   T* f = static_cast<T*>(p.dst);
-  const long long fx = (long long)p.ny * p.nz, fy = (long long)p.nx * p.nz,
-                  fz = (long long)p.nx * p.ny;
-  const long long total = 2 * (fx + fy + fz);
+  const long long ax = (long long)p.ny * p.nz, ay = (long long)p.nx * p.nz, az = (long long)p.nx * p.ny;
+  const long long total = 10 * (ax + ay + az);  // 2 faces x 5 directions per axis
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous step has completed
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
     long long r = k;
-    if (r < 2 * fx) {  // x faces
-      const int side = r >= fx;
-      r -= side * fx;
+    int face, x, y, z;
+    if (r < 10 * ax) {
+      face = (int)(r / (5 * ax));
+      r -= face * 5 * ax;
       y = (int)(r % p.ny);
-      z = (int)(r / p.ny);
-      x = side ? p.nx - 1 : 0;
-    } else if ((r -= 2 * fx) < 2 * fy) {  // y faces
-      const int side = r >= fy;
-      r -= side * fy;
+      z = (int)((r / p.ny) % p.nz);
+      x = face ? p.nx - 1 : 0;
+    } else if ((r -= 10 * ax) < 10 * ay) {
+      face = 2 + (int)(r / (5 * ay));
+      r -= (face - 2) * 5 * ay;
       x = (int)(r % p.nx);
-      z = (int)(r / p.nx);
-      y = side ? p.ny - 1 : 0;
-    } else {  // z faces
-      r -= 2 * fy;
-      const int side = r >= fz;
-      r -= side * fz;
+      z = (int)((r / p.nx) % p.nz);
+      y = face == 3 ? p.ny - 1 : 0;
+    } else {
+      r -= 10 * ay;
+      face = 4 + (int)(r / (5 * az));
+      r -= (face - 4) * 5 * az;
       x = (int)(r % p.nx);
-      y = (int)(r / p.nx);
-      z = side ? p.nz - 1 : 0;
+      y = (int)((r / p.nx) % p.ny);
+      z = face == 5 ? p.nz - 1 : 0;
     }
-#pragma unroll
-    for (int i = 1; i < NQ; i++) {
-      const int ux = x - cx(i), uy = y - cy(i), uz = z - cz(i);
-      if (ux >= 0 && ux < p.nx && uy >= 0 && uy < p.ny && uz >= 0 && uz < p.nz) continue;
-      const float v = aa_pull<S>(p, i, x, y, z);
-      const long long at = p.aa_parity == 0 ? aa_index(p, opp(i), ux, uy, uz) : aa_index(p, i, x, y, z);
-      if (!kCheckBounds || in_range(at, 1, p.aa_elems, p.state)) Store<S>::st(f + at, v);
-    }
+    const long long area = face < 2 ? ax : face < 4 ? ay : az;
+    const int i = aa_inward(face, (int)(r / area));
+    const float v = aa_pull<S>(p, i, x, y, z);
+    const long long at = p.aa_parity == 0 ? aa_index(p, opp(i), x - cx(i), y - cy(i), z - cz(i))
+                                          : aa_index(p, i, x, y, z);
+    if (!kCheckBounds || in_range(at, 1, p.aa_elems, p.state)) Store<S>::st(f + at, v);
   }
 }
 
@@ -110,7 +132,10 @@ __global__ void aa_fill_kernel(StepParams p) {
 struct AAStep {
   StepParams p;
   long long rd[NQ], wr[NQ];
-  int nunit, nxc, nzg;  // units: 128 x-cells x 2 z-rows at one y, numbered (y, z-group, x-chunk)
+  // units: 128 x-cells x 2 z-rows at one y, numbered (y, z-group, x-chunk),
+  // or with x-binned statistics over several chunks (y, x-chunk, z-group), so
+  // consecutive units of a block share their x-bins and flush less often
+  int nunit, nxc, nzg, xc_outer;
 };
 
 constexpr int AA_XT = 128, AA_ZR = 2;
@@ -119,13 +144,17 @@ constexpr int AA_XT = 128, AA_ZR = 2;
 // [b U / G, (b + 1) U / G); one thread per cell; plane statistics kept in
 // registers while the unit's row and x-bin stay the same.
 template <int S, bool STATS, bool VAR>
-__global__ void __launch_bounds__(AA_XT * AA_ZR, 2) aa_step_kernel(AAStep a) {
+__global__ void __launch_bounds__(AA_XT * AA_ZR, 3) aa_step_kernel(AAStep a) {
   using T = typename Store<S>::T;
   const StepParams& p = a.p;
   T* const f = static_cast<T*>(p.dst);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int lane = (ty * AA_XT + tx) & 31;
   __shared__ float s_gx;
+  // launched as a programmatic dependent of the fill (and the fill of the
+  // previous step): wait for it before touching memory
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (tx < 32 && ty == 0) {
     // bulk velocity of the previous step (exact fixed-point sum) for the controller;
     // block 0 clears the slot the next step accumulates into
@@ -168,9 +197,18 @@ __global__ void __launch_bounds__(AA_XT * AA_ZR, 2) aa_step_kernel(AAStep a) {
     qbin = -1;
   };
   for (long long u = u0; u < u1; u++) {
-    const int xc = (int)(u % a.nxc);
-    const long long r = u / a.nxc;
-    const int zg = (int)(r % a.nzg), y = (int)(r / a.nzg);
+    int xc, zg, y;
+    if (a.xc_outer) {
+      zg = (int)(u % a.nzg);
+      const long long r = u / a.nzg;
+      xc = (int)(r % a.nxc);
+      y = (int)(r / a.nxc);
+    } else {
+      xc = (int)(u % a.nxc);
+      const long long r = u / a.nxc;
+      zg = (int)(r % a.nzg);
+      y = (int)(r / a.nzg);
+    }
     const int x = xc * AA_XT + tx, z = zg * AA_ZR + ty;
     const bool active = x < p.nx && z < p.nz;
     const int bin = active ? (int)(((long long)x * p.nbins) / p.nx) : -1;

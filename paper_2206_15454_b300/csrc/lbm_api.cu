@@ -670,8 +670,9 @@ namespace {
 lbm_status aa_step(lbm_ctx* c) {
   const StepParams p = make_params(c);
   const lbm_grid& g = c->grid;
-  const long long faces = 2ll * ((long long)g.ny * g.nz + (long long)g.nx * g.nz + (long long)g.nx * g.ny);
-  const int fblocks = (int)std::max<long long>(1, std::min<long long>((faces + 255) / 256, c->sm_count * 8ll));
+  // one fill thread per (face cell, entering direction)
+  const long long fill = 10ll * ((long long)g.ny * g.nz + (long long)g.nx * g.nz + (long long)g.nx * g.ny);
+  const int fblocks = (int)std::max<long long>(1, std::min<long long>((fill + 255) / 256, c->sm_count * 16ll));
   AAStep a;
   a.p = p;
   const long long ys = c->ash.pitch, zs = (g.ny + 2) * ys, qs = (g.nz + 2) * zs;
@@ -689,6 +690,7 @@ lbm_status aa_step(lbm_ctx* c) {
   a.nxc = (g.nx + AA_XT - 1) / AA_XT;
   a.nzg = (g.nz + AA_ZR - 1) / AA_ZR;
   a.nunit = a.nxc * a.nzg * g.ny;
+  a.xc_outer = c->stats_on && c->nbins > 1 && a.nxc > 1;
   const int grid = (int)std::max<long long>(1, std::min<long long>(a.nunit, (long long)c->sm_count * c->blocks_per_sm));
   dispatch_s(c, [&](auto s) {
     KernAA<decltype(s)::value>::fill(fblocks, c->stream, p);

@@ -15,6 +15,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <climits>
 #include <stdint.h>
 
 namespace lbm {
@@ -1231,6 +1232,44 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           }
           last_x = x;
         }
+        // Ghost slots the pair feeds (as for one cell per thread): at most one
+        // for its c_x = +1 values (offset gro from `out`, cell grc) and one
+        // for its c_x = -1 values (glo, cell glc).  Cell x can be the first of
+        // its chunk or the last of the domain, cell x + 1 the last of its
+        // chunk or of the domain.  Only a two-cell last chunk of an outflow
+        // row needs both a chunk ghost and the outflow copy on the c_x = -1
+        // side: its copy is taken from the stored line below (copy1).
+        constexpr int kNone = INT_MIN;
+        int gro = kNone, glo = kNone;
+        bool grc = false, glc = false, copy1 = false;
+        if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
+          const long long own = (long long)(unsigned)(crow0 + xc) * Gm::ROW + 2 * tx;  // out - dst0
+          if (x == p.nx - 1) {
+            if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
+            else if (p.x_io == X_INOUT) glo = 1;
+          } else if (act1 && x + 1 == p.nx - 1) {
+            grc = glc = true;
+            if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
+            else if (p.x_io == X_INOUT) glo = 2;
+          } else if (act1 && tx == TPR - 1) {
+            grc = true;
+            gro = (int)((long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1 - own);
+          }
+          int left = kNone;
+          if (x == 0) {
+            if (p.x_io == X_PERIODIC) {
+              const int xl = p.nxc - 1;
+              left = (int)((long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT) - own);
+            }
+          } else if (tx == 0) {
+            left = (int)((long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT - own);
+          }
+          if (left != kNone) {
+            copy1 = glc && glo == 2;  // the outflow copy of cell x + 1 from the stored line
+            glo = left;
+            glc = false;
+          }
+        }
         collide_v<float2>(f, m, p.tau0, p.c18, [&](int i, float2 v) {
           T* o = out + i * Gm::XTP;
           if (act1) {
@@ -1238,48 +1277,13 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           } else {
             put1(o, v.x);
           }
+          if (cx(i) == 1 && gro != kNone) put1(o + gro, grc ? v.y : v.x);
+          if (cx(i) == -1 && glo != kNone) put1(o + glo, glc ? v.y : v.x);
         });
-        // ghost slots the two cells feed (as for one cell per thread: cell x can
-        // be the first of its chunk or the last of the domain, cell x + 1 the
-        // last of its chunk or of the domain), copied from the line just
-        // stored (edge lanes only; the pointers are not live in the collision)
-        T* gr0 = nullptr;
-        T* gl0 = nullptr;
-        T* gr1 = nullptr;
-        T* gl1 = nullptr;
-        if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
-          if (x == p.nx - 1) {
-            if (p.x_io == X_PERIODIC) gr0 = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
-            else if (p.x_io == X_INOUT) gl0 = out + 1;
-          }
-          if (act1 && x + 1 == p.nx - 1) {
-            if (p.x_io == X_PERIODIC) gr1 = dst0 + (long long)(unsigned)crow0 * Gm::ROW - 1;
-            else if (p.x_io == X_INOUT) gl1 = out + 2;
-          } else if (act1 && tx == TPR - 1) {
-            gr1 = dst0 + (long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1;
-          }
-          if (x == 0) {
-            if (p.x_io == X_PERIODIC) {
-              const int xl = p.nxc - 1;
-              gl0 = dst0 + (long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT);
-            }
-          } else if (tx == 0) {
-            gl0 = dst0 + (long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT;
-          }
-        }
-        if (gr0 || gl0 || gr1 || gl1) {
+        if (copy1) {
 #pragma unroll
-          for (int i = 0; i < NQ; i++) {
-            const T* o = out + i * Gm::XTP;
-            if (cx(i) == 1) {
-              if (gr0) put1(gr0 + i * Gm::XTP, Store<S>::to_float(__ldcg(o)));
-              if (gr1) put1(gr1 + i * Gm::XTP, Store<S>::to_float(__ldcg(o + 1)));
-            }
-            if (cx(i) == -1) {
-              if (gl0) put1(gl0 + i * Gm::XTP, Store<S>::to_float(__ldcg(o)));
-              if (gl1) put1(gl1 + i * Gm::XTP, Store<S>::to_float(__ldcg(o + 1)));
-            }
-          }
+          for (int i = 0; i < NQ; i++)
+            if (cx(i) == -1) put1(out + 2 + i * Gm::XTP, Store<S>::to_float(__ldcg(out + 1 + i * Gm::XTP)));
         }
         if (p.io_one && x == p.nx - 1) {
           // a one-cell last chunk at an outflow (its cell is the pair's first):

@@ -22,7 +22,23 @@ VARIANTS = {
     "rho2": dict(sgs_rho_power=2),
     "all": dict(drag_streamwise_only=1, forcing_scheme=1, sgs_rho_power=2),
 }
+
+
+def strong_forcing_box():
+    """A periodic box with strong driving, very dense Gaussian canopy (C_D a up to
+    3 per cell), C_s = 0.3 and 10 % velocity perturbations: accelerations of
+    1e-3..1e-2 per step and density varying by about 1 %, where each variant
+    changes the state by more than 1e-5 within 100 steps (exact-difference and
+    Guo forcing differ at O(g^2); the rho power matters through rho - 1)."""
+    ny = 8
+    return W.Case("strong_forcing_box", 16, ny, 8, bc_y=(W.PERIODIC, W.PERIODIC), tau0=0.51,
+                  cs=0.3, g=(2e-3, 5e-4, -3e-4), cd=0.15, canopy_x=(2, 14),
+                  lad=W.lad_gaussian(ny, 20.0, 8.0), seed=21, init_perturb=0.1,
+                  u_profile=np.full(ny, 0.08))
+
+
 CASES = [
+    strong_forcing_box(),
     SMALL[2],                                             # canopy, inflow/outflow, x-bins
     SMALL[3],                                             # ragged channel + canopy, controller
     SMALL[6],                                             # periodic box, 3-component driving, Gaussian LAD
@@ -53,7 +69,7 @@ def test_variants_change_the_flow():
     from the default one by more than twice the FP32 parity bound (1e-6), so a
     kernel that ignored the flag would fail the variant parity test above
     (the measured FP32 error is about 1e-7)."""
-    base = SMALL[6]
+    base = strong_forcing_box()
     d0 = P.Domain(base)
     d0.step(100)
     f0 = d0.get_f()
