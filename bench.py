@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-canopy", action="store_true",
                     help="skip the 512x128x256 canopy leg (x-binned statistics)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--learned-window", default="1000,1000", metavar="SPINUP,AVERAGE",
+                    help="coarse steps before and during averaging in the learned leg")
     ap.add_argument("--profile", metavar="NXxNYxNZ|canopy|ensemble|learned", default=None,
                     help="run a few steps of the channel workload at this size (or of the "
                          "64-box ensemble, or of a 256x64x128 canopy domain with the learned "
@@ -68,16 +70,25 @@ def code_tokens(text: str) -> str:
     return " ".join(text.split())
 
 
-def kernel_source_hash(text=None):
-    """Hash of the step kernel's code (lbm_device.cuh: the kernel, its tile
-    loop and launch-independent constants; comments and layout do not count),
-    to tell whether the profiles/ counters still apply."""
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_aa.cuh", "lbm_kern.inc")
+
+
+def kernel_source_hash(texts=None):
+    """Hash of the step kernels' code (lbm_device.cuh: the pull kernel, its
+    tile loop and collision; lbm_aa.cuh: the AA kernels; lbm_kern.inc: their
+    instantiations and launch shapes; comments and layout do not count), to
+    tell whether the profiles/ counters still apply."""
     import hashlib
 
-    if text is None:
-        with open(os.path.join(ROOT, "paper_2206_15454_b300", "csrc", "lbm_device.cuh")) as fh:
-            text = fh.read()
-    return hashlib.sha256(b"lbm_device.cuh" + code_tokens(text).encode()).hexdigest()[:16]
+    if texts is None:
+        texts = []
+        for name in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, "paper_2206_15454_b300", "csrc", name)) as fh:
+                texts.append(fh.read())
+    h = hashlib.sha256()
+    for name, text in zip(KERNEL_SOURCES, texts):
+        h.update(name.encode() + b"\0" + code_tokens(text).encode() + b"\0")
+    return h.hexdigest()[:16]
 
 
 def measured_traffic_rw(storage_name, cells, workload="channel"):
@@ -319,25 +330,39 @@ def time_canopy(P, W, steps, warmup, hbm):
     return out
 
 
-def time_learned(P, W, steps, warmup):
-    """The learned first-layer correction: (1) its gain on a 64x32x32 canopy
-    boundary layer (trained on the plain coarse and 2x-fine runs, error of the
-    mean streamwise velocity against the coarsened fine run), (2) throughput
-    of the 1024x256x512 canopy domain (h = 12, a = 0.25, C_D = 0.15,
-    inflow/outflow, FP32) with and without the correction in every step."""
+def time_learned(P, W, steps, warmup, spinup=1000, average=1000):
+    """The learned first-layer correction at its full size: the 1024x256x512
+    canopy domain (h = 12, a = 0.25, C_D = 0.15, inflow/outflow, FP32) and the
+    same set-up on the 2x finer 2048x512x1024 grid (1.07 G cells, FP32 in the
+    in-place AA layout: 82 GB).  (1) Both plain runs for the same physical time
+    (spinup + average coarse steps; the fine run takes twice as many), the
+    network trained on the coarse run's column features against the fine run's
+    first-cell deficits, and the gain: error of the coarse mean streamwise
+    velocity against the coarsened fine run, plain and corrected (lowest 1, 6
+    and 12 rows = first cell, half canopy, canopy layer); (2) throughput of the
+    coarse domain with and without the correction in every step."""
     import torch
 
     from paper_2206_15454_b300 import learned as L
 
-    small = W.canopy_abl(64, 32, 32, h=6.0, a=0.25, cd=0.15, canopy_x0=16, xbin=1)
-    ref = L.reference_runs(small, 2000, 2000, sample_every=20)
-    net, l0, l1 = L.train_correction(ref, epochs=30)
-    plain, corr = L.corrected_run(small, net, 0.01, 2000, 2000)
+    case = W.canopy_abl(1024, 256, 512, h=12.0, a=0.25, cd=0.15, canopy_x0=256, xbin=16)
+    fine_storage = P.LBM_F32 | P.LBM_STORAGE_AA
+    t_ref = time.perf_counter()
+    ref = L.reference_runs(case, spinup, average, sample_every=50, fine_storage=fine_storage)
+    t_ref = time.perf_counter() - t_ref
+    torch.cuda.empty_cache()
+    t_train = time.perf_counter()
+    net, l0, l1 = L.train_correction(ref, epochs=4, batch=4096)
+    t_train = time.perf_counter() - t_train
+    n_samples = int(ref.features.shape[0])
+    t_corr = time.perf_counter()
+    plain, corr = L.corrected_run(case, net, 0.01, spinup, average, plain=ref.coarse)
+    t_corr = time.perf_counter() - t_corr
     gain = {f"rows_{r}": {"plain": round(L.profile_error(plain, ref.fine_coarsened, r), 4),
                           "corrected": round(L.profile_error(corr, ref.fine_coarsened, r), 4)}
             for r in (1, 6, 12)}
+    del ref
 
-    case = W.canopy_abl(1024, 256, 512, h=12.0, a=0.25, cd=0.15, canopy_x0=256, xbin=16)
     d = P.Domain(case, P.LBM_F32)
     out = {}
     for label, use in (("plain", False), ("corrected", True)):
@@ -355,14 +380,20 @@ def time_learned(P, W, steps, warmup):
         out[label] = {"value": round(case.cells / ms / 1e3, 1), "unit": "MLUPS", "ms_per_step": ms}
     d.close()
     net.close()
+    torch.cuda.empty_cache()
+    fine = L.refine(case)
     return {"workload": "canopy ABL 1024x256x512 (h=12, a=0.25, C_D=0.15, inflow/outflow), FP32",
             "cells": case.cells, "steps": steps, **out,
             "correction_share_of_step": round(1 - out["plain"]["ms_per_step"] /
                                               out["corrected"]["ms_per_step"], 4),
-            "gain": {"workload": "canopy ABL 64x32x32 (h=6) vs the same on 128x64x64, "
-                                 "2000 + 2000 steps, lam = 0.01",
-                     "training_loss": [round(l0, 4), round(l1, 4)],
-                     "mean_u_rel_l2_vs_coarsened_fine": gain}}
+            "gain": {"workload": f"the same on {fine.nx}x{fine.ny}x{fine.nz} ({fine.cells} cells, "
+                                 f"FP32 AA storage) coarsened; {spinup} + {average} coarse steps "
+                                 f"({2 * spinup} + {2 * average} fine), lam = 0.01",
+                     "training": {"samples": n_samples, "epochs": 4, "batch": 4096,
+                                  "loss_first_last_epoch": [round(l0, 4), round(l1, 4)]},
+                     "mean_u_rel_l2_vs_coarsened_fine": gain,
+                     "seconds": {"plain_runs": round(t_ref, 1), "training": round(t_train, 1),
+                                 "corrected_run": round(t_corr, 1)}}}
 
 
 def e2e_run(P, d, steps):
@@ -524,7 +555,9 @@ def time_aa(P, W, steps, warmup, hbm, ws):
         out[name] = {"value": round(case.cells * steps * ws / (tot * 1e-3) / 1e6, 1),
                      "unit": "MLUPS", "ms_per_step": tot / steps,
                      "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
-                                  "unit": "GB/s", "frac": round(ach / hbm, 4)},
+                                  "unit": "GB/s", "frac": round(ach / hbm, 4),
+                                  "traffic": measured_traffic(name + "-aa", case.cells),
+                                  "traffic_read_write": measured_traffic_rw(name + "-aa", case.cells)},
                      "workspace_bytes": P.lbm_workspace_bytes(g, st, 1),
                      "workspace_bytes_pull": P.lbm_workspace_bytes(g, P.STORAGE_NAMES[name], 1)}
     return out
@@ -635,7 +668,9 @@ def run_ours(args):
     if not args.no_ensemble:
         res["ensemble"] = time_ensemble(P, W, min(args.steps, 1000), max(args.warmup, 3), hbm)
     if not args.no_learned:
-        res["learned"] = time_learned(P, W, min(args.steps, 100), max(min(args.warmup, 10), 3))
+        spin, avg = (int(v) for v in args.learned_window.split(","))
+        res["learned"] = time_learned(P, W, min(args.steps, 100), max(min(args.warmup, 10), 3),
+                                      spin, avg)
     if ref is not None and not args.no_canopy:
         res["canopy"]["profile_error_vs_fp64_oracle"] = canopy_profile_errors(P, ref)
     if rank == 0:

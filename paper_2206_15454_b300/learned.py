@@ -93,15 +93,17 @@ def coarsen_means(fine_stats):
 
 
 def reference_runs(case, spinup: int, average: int, sample_every: int = 20,
-                   storage=LBM_F32) -> Reference:
+                   storage=LBM_F32, fine_storage=None) -> Reference:
     """Run the plain method on `case` (coarse) and on refine(case) for the same
     physical time, average their profiles per x-bin, and collect the coarse
     run's column features every `sample_every` steps of the averaging window,
-    each paired with the deficits of its x-bin."""
+    each paired with the deficits of its x-bin.  The fine run may use another
+    storage (fine_storage; e.g. the in-place AA layout, which halves the
+    memory of a grid with eight times the cells)."""
     fine_case = refine(case)
     nb = case.stats_xbins
     assert fine_case.stats_xbins == nb and case.nx % nb == 0
-    fine = Domain(fine_case, storage)
+    fine = Domain(fine_case, storage if fine_storage is None else fine_storage)
     fine.step(2 * spinup)
     fine.stats_reset(True)
     fine.step(2 * average)
@@ -141,11 +143,14 @@ def train_correction(ref: Reference, epochs: int = 40, batch: int = 1024, lr: fl
     return net, l0, l1
 
 
-def corrected_run(case, net, lam: float, spinup: int, average: int, storage=LBM_F32):
+def corrected_run(case, net, lam: float, spinup: int, average: int, storage=LBM_F32,
+                  plain=None):
     """Statistics of the coarse run with the correction on (from the start of
-    the averaging window), and of the same run without it."""
-    out = []
-    for use in (False, True):
+    the averaging window), and of the same run without it (`plain`: those
+    statistics already taken, e.g. Reference.coarse of the same case, window and
+    storage, which the deterministic step reproduces)."""
+    out = [] if plain is None else [plain]
+    for use in ((False, True) if plain is None else (True,)):
         d = Domain(case, storage)
         d.step(spinup)
         if use:

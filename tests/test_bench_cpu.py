@@ -11,10 +11,17 @@ __device__ int f(int a) {  /* block
 
 
 def test_code_hash_ignores_comments_and_layout_but_not_code():
-    h = bench.kernel_source_hash(SRC)
-    assert bench.kernel_source_hash(SRC.replace("// a comment", "// another comment")) == h
-    assert bench.kernel_source_hash(SRC.replace("\n", "\n\n")) == h
-    assert bench.kernel_source_hash(SRC.replace("a + 1", "a + 2")) != h
+    def h(src, k=0):  # the source in slot k of the hashed files
+        texts = [""] * len(bench.KERNEL_SOURCES)
+        texts[k] = src
+        return bench.kernel_source_hash(texts)
+
+    for k in range(len(bench.KERNEL_SOURCES)):
+        base = h(SRC, k)
+        assert h(SRC.replace("// a comment", "// another comment"), k) == base
+        assert h(SRC.replace("\n", "\n\n"), k) == base
+        assert h(SRC.replace("a + 1", "a + 2"), k) != base
+    assert h(SRC, 0) != h(SRC, 1)  # which file holds the code counts
 
 
 def test_traffic_scales_with_cells_and_is_near_the_algorithmic_bytes():
