@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(AA_XT * AA_ZR, 3) aa_step_kernel(AAStep a) {
         m = moments<VAR>(fi, gx, gy, gz, kd, p.drag_x_only);
         collide<VAR>(fi, m, p.tau0, p.c18, p.edm, p.tau_rho2, put);
       } else {  // the default model: the same arithmetic as the pull kernel
-        const MacroV<float> mv = moments_v<float>(fi, gx, gy, gz, kd, kd > 0.f);
-        collide_v<float>(fi, mv, p.tau0, p.c18, put);
+        const MacroV<float> mv = moments_v<float>(fi, gx, gy, gz, kd, kd > 0.f, p.tau0, p.c18);
+        collide_v<float>(fi, mv, put);
         m = Macro{mv.drho, mv.rho, mv.ux, mv.uy, mv.uz, mv.Fx, mv.Fy, mv.Fz};
       }
       ub_fix += __float2ll_rn(m.ux * 4294967296.0f);

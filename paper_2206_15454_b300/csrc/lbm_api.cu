@@ -308,6 +308,7 @@ StepParams make_params(const lbm_ctx* c) {
   p.ctr_slot = (int)(c->steps & 1);
   p.stats = c->stats();
   p.nbins = c->nbins;
+  p.bins_even = c->nbins > 0 && g.nx % c->nbins == 0 && (g.nx / c->nbins) % 2 == 0;
   p.xc_outer = c->stats_on && c->nbins > 1 && c->sh.nxc > 1;
   p.t_in = p.xc_outer ? p.nzg : p.nxc;
   p.t_mid = p.xc_outer ? p.nxc : p.nzg;
@@ -389,7 +390,7 @@ StagePlan stage_plan(int cpt) {
   StagePlan sp;
   sp.block = dim3(XT / cpt, 256 * cpt / XT, 1);
   const size_t stage = (size_t)sp.block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
-  const size_t budget = cpt == 1 ? 62 * 1024 : 100 * 1024;
+  const size_t budget = 62 * 1024;
   sp.nstage = (int)std::max<size_t>(2, std::min<size_t>(8, budget / stage));
   sp.smem = sp.nstage * stage;
   return sp;

@@ -73,6 +73,22 @@ template <> struct Store<1> {
   static __device__ __forceinline__ void st2(T* p, float2 v) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.x, v.y);
   }
+  // the two values of a packed word (low half first); unpack2_again is the
+  // same conversion, written so the compiler does not merge it with an earlier
+  // unpack2 of the same word (the collision converts again rather than keep
+  // 19 more registers alive)
+  static __device__ __forceinline__ float2 unpack2(uint32_t r) {
+    float2 v;
+    asm("{.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;}"
+        : "=f"(v.x), "=f"(v.y) : "r"(r));
+    return v;
+  }
+  static __device__ __forceinline__ float2 unpack2_again(uint32_t r) {
+    float2 v;
+    asm volatile("{.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;}"
+                 : "=f"(v.x), "=f"(v.y) : "r"(r));
+    return v;
+  }
 };
 template <> struct Store<2> {
   using T = __nv_bfloat16;
@@ -85,6 +101,15 @@ template <> struct Store<2> {
   }
   static __device__ __forceinline__ void st2(T* p, float2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+  }
+  // a BF16 value is the high half of the FP32 value with the same bits
+  static __device__ __forceinline__ float2 unpack2(uint32_t r) {
+    return make_float2(__uint_as_float(r << 16), __uint_as_float(r & 0xffff0000u));
+  }
+  static __device__ __forceinline__ float2 unpack2_again(uint32_t r) {
+    uint32_t lo, hi;
+    asm volatile("{\n\tshl.b32 %0, %2, 16;\n\tand.b32 %1, %2, 0xffff0000;\n\t}" : "=r"(lo), "=r"(hi) : "r"(r));
+    return make_float2(__uint_as_float(lo), __uint_as_float(hi));
   }
 };
 
@@ -175,6 +200,7 @@ struct StepParams {
   // statistics
   double* stats;            // [9][nbins][ny] FP64 sums
   int nbins;
+  int bins_even;            // x-bins of one even width: cells x, x + 1 (x even) share their bin
   DevState* state;
   // learned first-layer correction: extra (x, z) acceleration of the cells at
   // y = 0, per column [z][x], or nullptr
@@ -485,22 +511,30 @@ struct VOps<float2> {
 template <class V>
 struct MacroV {
   V drho, rho, ux, uy, uz, Fx, Fy, Fz;
+  V om;  // 1 / tau_total
 };
 
 // Eqs. density and momentum with the driving acceleration and the canopy
 // drag solved jointly (as moments()).  k: C_D a(y) per cell; a cell with
 // k = 0 keeps u and F as without drag (selected, so two cells side by side
-// give what each gives alone).
-template <class V>
-__device__ __forceinline__ MacroV<V> moments_v(const V* f, V gx, V gy, V gz, V k, bool any_drag) {
+// give what each gives alone).  fg(i) gives f_i - w_i.  Also the relaxation
+// rate 1/tau_total (Eqs. nu_t, strain, tau_total) from Pi_neq (Eq. tensor),
+// which follows from the second moments S of f - w (the same pair sums): the
+// second moment of the D3Q19 equilibrium is rho c_s^2 I + rho u u exactly
+// (the lattice is isotropic to fourth order) and sum_i c_i c_i w_i = c_s^2 I,
+// so Pi_neq = sum_i c_i c_i (f_i - f_eq_i) = S - c_s^2 drho I - rho u u.
+template <class V, class Get>
+__device__ __forceinline__ MacroV<V> moments_g(Get&& fg, V gx, V gy, V gz, V k, bool any_drag,
+                                               float tau0, float c18) {
   using O = VOps<V>;
   V sm[NQ], df[NQ];
 #pragma unroll
   for (int i = 1; i < NQ; i += 2) {
-    sm[i] = O::add(f[i], f[i + 1]);
-    df[i] = O::sub(f[i], f[i + 1]);
+    const V a = fg(i), b = fg(i + 1);
+    sm[i] = O::add(a, b);
+    df[i] = O::sub(a, b);
   }
-  V drho = f[0];
+  V drho = fg(0);
 #pragma unroll
   for (int i = 1; i < NQ; i += 2) drho = O::add(drho, sm[i]);
   // odd directions 1 (+x), 3 (+y), 5 (+z), 7 (+x+y), 9 (+x-y), 11 (+x+z),
@@ -508,6 +542,12 @@ __device__ __forceinline__ MacroV<V> moments_v(const V* f, V gx, V gy, V gz, V k
   const V mx = O::add(O::add(O::add(O::add(df[1], df[7]), df[9]), df[11]), df[13]);
   const V my = O::add(O::add(O::sub(O::add(df[3], df[7]), df[9]), df[15]), df[17]);
   const V mz = O::sub(O::add(O::sub(O::add(df[5], df[11]), df[13]), df[15]), df[17]);
+  const V sxx = O::add(O::add(O::add(O::add(sm[1], sm[7]), sm[9]), sm[11]), sm[13]);
+  const V syy = O::add(O::add(O::add(O::add(sm[3], sm[7]), sm[9]), sm[15]), sm[17]);
+  const V szz = O::add(O::add(O::add(O::add(sm[5], sm[11]), sm[13]), sm[15]), sm[17]);
+  const V sxy = O::sub(sm[7], sm[9]);
+  const V sxz = O::sub(sm[11], sm[13]);
+  const V syz = O::sub(sm[15], sm[17]);
   MacroV<V> m;
   m.drho = drho;
   m.rho = O::add(O::c(1.0f), drho);
@@ -536,7 +576,27 @@ __device__ __forceinline__ MacroV<V> moments_v(const V* f, V gx, V gy, V gz, V k
   m.ux = vx;
   m.uy = vy;
   m.uz = vz;
+  const V nr = O::mul(O::c(-1.0f), m.rho);
+  const V nrux = O::mul(nr, vx), nruy = O::mul(nr, vy);
+  const V d3 = O::mul(O::c(1.0f / 3.0f), drho);
+  const V pxx = O::fma(nrux, vx, O::sub(sxx, d3));
+  const V pyy = O::fma(nruy, vy, O::sub(syy, d3));
+  const V pzz = O::fma(O::mul(nr, vz), vz, O::sub(szz, d3));
+  const V pxy = O::fma(nrux, vy, sxy);
+  const V pxz = O::fma(nrux, vz, sxz);
+  const V pyz = O::fma(nruy, vz, syz);
+  const V off = O::fma(pxy, pxy, O::fma(pxz, pxz, O::mul(pyz, pyz)));
+  const V q2 = O::fma(pxx, pxx, O::fma(pyy, pyy, O::fma(pzz, pzz, O::mul(O::c(2.0f), off))));
+  const V arg = O::add(O::c(tau0 * tau0), O::div(O::mul(O::c(c18), O::sqrt(q2)), m.rho));
+  const V tau = O::mul(O::c(0.5f), O::add(O::c(tau0), O::sqrt(arg)));
+  m.om = O::div(O::c(1.0f), tau);
   return m;
+}
+
+template <class V>
+__device__ __forceinline__ MacroV<V> moments_v(const V* f, V gx, V gy, V gz, V k, bool any_drag,
+                                               float tau0, float c18) {
+  return moments_g<V>([&](int i) { return f[i]; }, gx, gy, gz, k, any_drag, tau0, c18);
 }
 
 // BGK-Smagorinsky collision with Guo forcing (as collide()), per pair
@@ -550,54 +610,40 @@ __device__ __forceinline__ V pair_dot(int i, V ax, V ay, V az) {
        : O::sub(ay, az);
 }
 
-template <class V, class Emit>
-__device__ __forceinline__ void collide_v(const V* f, const MacroV<V>& m, float tau0, float c18,
-                                          Emit&& emit) {
+// Relaxation (Eqs. lbe, bgk) at the rate m.om of moments_g, plus Guo's
+// forcing term; fg(i) gives f_i - w_i again.
+template <class V, class Get, class Emit>
+__device__ __forceinline__ void collide_g(Get&& fg, const MacroV<V>& m, Emit&& emit) {
   using O = VOps<V>;
   const V ux = m.ux, uy = m.uy, uz = m.uz;
   const V uu = O::fma(ux, ux, O::fma(uy, uy, O::mul(uz, uz)));
   const V base = O::fma(O::mul(O::c(-1.5f), m.rho), uu, m.drho);  // drho - 1.5 rho u.u
   const V r45 = O::mul(O::c(4.5f), m.rho);
   const V r3 = O::mul(O::c(3.0f), m.rho);
-  V pxx, pyy, pzz, pxy, pxz, pyz;  // Pi_neq (Eq. tensor) from the pair sums, summed in i order
-#pragma unroll
-  for (int i = 1; i < NQ; i += 2) {
-    const V e = pair_dot<V>(i, ux, uy, uz);
-    const V sym = O::mul(O::c(wgt(i)), O::fma(O::mul(r45, e), e, base));  // even part of f_eq - w
-    const V np = O::fma(O::c(-2.0f), sym, O::add(f[i], f[i + 1]));  // pair sum of f - f_eq
-    if (i == 1) pxx = np; else if (cx(i) != 0) pxx = O::add(pxx, np);
-    if (i == 3) pyy = np; else if (cy(i) != 0) pyy = O::add(pyy, np);
-    if (i == 5) pzz = np; else if (cz(i) != 0) pzz = O::add(pzz, np);
-    if (i == 7) pxy = np;
-    if (i == 9) pxy = O::sub(pxy, np);
-    if (i == 11) pxz = np;
-    if (i == 13) pxz = O::sub(pxz, np);
-    if (i == 15) pyz = np;
-    if (i == 17) pyz = O::sub(pyz, np);
-  }
-  const V off = O::fma(pxy, pxy, O::fma(pxz, pxz, O::mul(pyz, pyz)));
-  const V q2 = O::fma(pxx, pxx, O::fma(pyy, pyy, O::fma(pzz, pzz, O::mul(O::c(2.0f), off))));
-  const V arg = O::add(O::c(tau0 * tau0), O::div(O::mul(O::c(c18), O::sqrt(q2)), m.rho));
-  const V tau = O::mul(O::c(0.5f), O::add(O::c(tau0), O::sqrt(arg)));
-  const V om = O::div(O::c(1.0f), tau);
+  const V om = m.om;
   const V keep = O::sub(O::c(1.0f), om);
   const V pre = O::fma(O::c(-0.5f), om, O::c(1.0f));
   const V uF3 = O::mul(O::c(3.0f), O::fma(ux, m.Fx, O::fma(uy, m.Fy, O::mul(uz, m.Fz))));
   {
     const V pw = O::mul(pre, O::c(wgt(0)));
-    emit(0, O::fma(keep, f[0], O::fma(om, O::mul(O::c(wgt(0)), base), O::neg(O::mul(pw, uF3)))));
+    emit(0, O::fma(keep, fg(0), O::fma(om, O::mul(O::c(wgt(0)), base), O::neg(O::mul(pw, uF3)))));
   }
 #pragma unroll
   for (int i = 1; i < NQ; i += 2) {
     const V e = pair_dot<V>(i, ux, uy, uz);
     const V h = pair_dot<V>(i, m.Fx, m.Fy, m.Fz);
-    const V sym = O::mul(O::c(wgt(i)), O::fma(O::mul(r45, e), e, base));  // recomputed: fewer live registers
+    const V sym = O::mul(O::c(wgt(i)), O::fma(O::mul(r45, e), e, base));  // even part of f_eq - w
     const V pw = O::mul(pre, O::c(wgt(i)));
     const V even = O::fma(om, sym, O::mul(pw, O::fma(O::mul(O::c(9.0f), e), h, O::neg(uF3))));
     const V odd = O::fma(om, O::mul(O::mul(O::c(wgt(i)), r3), e), O::mul(O::mul(O::c(3.0f), pw), h));
-    emit(i, O::fma(keep, f[i], O::add(even, odd)));
-    emit(i + 1, O::fma(keep, f[i + 1], O::sub(even, odd)));
+    emit(i, O::fma(keep, fg(i), O::add(even, odd)));
+    emit(i + 1, O::fma(keep, fg(i + 1), O::sub(even, odd)));
   }
+}
+
+template <class V, class Emit>
+__device__ __forceinline__ void collide_v(const V* f, const MacroV<V>& m, Emit&& emit) {
+  collide_g<V>([&](int i) { return f[i]; }, m, emit);
 }
 
 __device__ __forceinline__ float drag_factor(const StepParams& p, int x, int y) {
@@ -1067,7 +1113,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         if (VAR) {
           m = moments<VAR>(f, gxc, gy, gzc, kd, p.drag_x_only);
         } else {
-          mv = moments_v<float>(f, gxc, gy, gzc, kd, kd > 0.f);
+          mv = moments_v<float>(f, gxc, gy, gzc, kd, kd > 0.f, p.tau0, p.c18);
           m = Macro{mv.drho, mv.rho, mv.ux, mv.uy, mv.uz, mv.Fx, mv.Fy, mv.Fz};
         }
       }
@@ -1116,7 +1162,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           if (cx(i) == -1 && gl) Store<S>::st(gl + i * Gm::XTP, v);
         };
         if (VAR) collide<VAR>(f, m, p.tau0, p.c18, p.edm, p.tau_rho2, put);
-        else collide_v<float>(f, mv, p.tau0, p.c18, put);
+        else collide_v<float>(f, mv, put);
         if (p.io_one && x == p.nx - 1) {
           // a one-cell last chunk at an outflow: gl went to the previous
           // chunk's right ghost, so the zero-gradient copy beside the cell is
@@ -1151,32 +1197,38 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         stat_xc = xc;
       }
 
-      float2 f[NQ];
+      // the 19 populations of cells x and x + 1 as packed words of the
+      // storage type (low half: cell x), converted to FP32 by the moments and
+      // again by the collision: 19 registers instead of 38
+      uint32_t raw[NQ] = {};
       MacroV<float2> m;
+      const bool eqtop = p.y_walls && p.top == 3 && y == p.ny - 1;
+      auto f_at = [&](int i, bool again) -> float2 {
+        if (cy(i) == -1 && eqtop) return make_float2(p.feq_top[i], p.feq_top[i]);
+        return again ? Store<S>::unpack2_again(raw[i]) : Store<S>::unpack2(raw[i]);
+      };
       if (active) {
         const T* sm = reinterpret_cast<const T*>(stage) + threadIdx.y * NQ * St::SROW + St::H + 2 * tx;
+        const unsigned short* sh = reinterpret_cast<const unsigned short*>(sm);
         // streaming from the staged rows: rows with c_x = 0 hold the pair at an
         // aligned offset (one 32-bit load), the others one cell to the side
+        // (two 16-bit loads); at a wall the own column (bounce-back) or, at a
+        // free-slip top, the staged row that is already the mirrored one
   #pragma unroll
         for (int i = 0; i < NQ; i++) {
-          if (cx(i) == 0) {
-            f[i] = Store<S>::ld2(sm + i * St::SROW);
-          } else {
-            f[i].x = Store<S>::to_float(sm[i * St::SROW - cx(i)]);
-            f[i].y = Store<S>::to_float(sm[i * St::SROW + 1 - cx(i)]);
-          }
+          if (cx(i) == 0) raw[i] = *reinterpret_cast<const uint32_t*>(sm + i * St::SROW);
+          else raw[i] = __byte_perm(sh[i * St::SROW - cx(i)], sh[i * St::SROW + 1 - cx(i)], 0x5410);
         }
         if (p.y_walls) {
           if (y == 0) {
   #pragma unroll
             for (int i = 0; i < NQ; i++)
-              if (cy(i) == 1) f[i] = Store<S>::ld2(sm + i * St::SROW);
+              if (cy(i) == 1) raw[i] = *reinterpret_cast<const uint32_t*>(sm + i * St::SROW);
           }
-          if (y == p.ny - 1 && p.top != 2) {
+          if (y == p.ny - 1 && p.top == 1) {
   #pragma unroll
             for (int i = 0; i < NQ; i++)
-              if (cy(i) == -1)
-                f[i] = p.top == 1 ? Store<S>::ld2(sm + i * St::SROW) : make_float2(p.feq_top[i], p.feq_top[i]);
+              if (cy(i) == -1) raw[i] = *reinterpret_cast<const uint32_t*>(sm + i * St::SROW);
           }
         }
         float2 gxc = make_float2(gx, gx), gzc = make_float2(gz, gz);
@@ -1187,7 +1239,8 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           gzc = make_float2(gz + a0.y, gz + a1.y);
         }
         const float2 kd = make_float2(drag_factor(p, x, y), drag_factor(p, x + 1, y));
-        m = moments_v<float2>(f, gxc, make_float2(gy, gy), gzc, kd, kd.x > 0.f || kd.y > 0.f);
+        m = moments_g<float2>([&](int i) { return f_at(i, false); }, gxc, make_float2(gy, gy), gzc, kd,
+                              kd.x > 0.f || kd.y > 0.f, p.tau0, p.c18);
       }
       // release the stage: the moments consumed every staged value of this warp
       __syncwarp();
@@ -1208,7 +1261,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         }
         if (STATS) {
           const float2 u = m.ux, v = m.uy, w = m.uz;
-          const bool split = act1 && p.nbins > 1 &&
+          const bool split = act1 && p.nbins > 1 && !p.bins_even &&
                              ((long long)x * p.nbins) / p.nx != ((long long)(x + 1) * p.nbins) / p.nx;
           if (act1 && !split) {  // both cells in the thread's sums
             qs[0 * 256] += u.x + u.y; qs[1 * 256] += v.x + v.y; qs[2 * 256] += w.x + w.y;
@@ -1270,7 +1323,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
             glc = false;
           }
         }
-        collide_v<float2>(f, m, p.tau0, p.c18, [&](int i, float2 v) {
+        collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
           T* o = out + i * Gm::XTP;
           if (act1) {
             if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
@@ -1320,7 +1373,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 // VAR: the model-variant form (flags in p); the default form has none of
 // their code.
 template <int XT, int S, bool STATS, bool VAR, int CPT>
-__global__ void __launch_bounds__(256, CPT == 1 ? 3 : 2) step_kernel(StepParams p) {
+__global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
   step_tiles<XT, S, STATS, VAR, CPT>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
                                      blockIdx.x, true);
 }
@@ -1334,7 +1387,7 @@ struct BatchWork {
 };
 
 template <int XT, int S, bool STATS, int CPT>
-__global__ void __launch_bounds__(256, CPT == 1 ? 3 : 2) batch_step_kernel(
+__global__ void __launch_bounds__(256, 3) batch_step_kernel(
     const StepParams* __restrict__ boxes, const BatchWork* __restrict__ work) {
   __shared__ __align__(16) StepParams s_p;
   const BatchWork w = work[blockIdx.x];

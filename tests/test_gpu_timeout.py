@@ -15,8 +15,10 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("storage", [P.LBM_F32, P.LBM_F16_SHIFTED])
 @pytest.mark.parametrize("fill", [0, 1, 5])
 def test_a_withheld_fill_times_out_and_is_reported(storage, fill):
-    # 4096 tiles: every block's first eight fills are tiles of its static run
-    case = W.channel_les(256, 64, 64)
+    # 8192 tiles (FP16: two rows per tile) or 16384 (FP32) over at most
+    # 148 x 3 blocks: every block's static run is at least 16 tiles long, so
+    # the withheld fill is always one of block 0's static fills
+    case = W.channel_les(256, 128, 128)
     d = P.Domain(case, storage)
     d.step(2)
     d.sync()
