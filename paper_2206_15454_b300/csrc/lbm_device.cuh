@@ -497,7 +497,15 @@ template <>
 struct VOps<float2> {
   static __device__ __forceinline__ float2 c(float a) { return make_float2(a, a); }
   static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, neg(b)); }
+  // one packed subtraction (rounded like add(a, -b))
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+  }
   static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
   static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 d) { return __ffma2_rn(a, b, d); }
   static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
@@ -565,7 +573,7 @@ __device__ __forceinline__ MacroV<V> moments_g(Get&& fg, V gx, V gy, V gz, V k, 
     const V vn = O::sqrt(O::fma(vx, vx, O::fma(vy, vy, O::mul(vz, vz))));
     const V s = O::div(O::c(2.0f), O::add(O::c(1.0f), O::sqrt(O::fma(O::mul(O::c(2.0f), k), vn, O::c(1.0f)))));
     const V ux = O::mul(vx, s), uy = O::mul(vy, s), uz = O::mul(vz, s);
-    const V rk = O::neg(O::mul(m.rho, O::mul(O::mul(k, s), vn)));  // -rho k |u|
+    const V rk = O::mul(O::mul(O::c(-1.0f), m.rho), O::mul(O::mul(k, s), vn));  // -rho k |u|
     m.Fx = O::where_pos(k, O::fma(rk, ux, m.Fx), m.Fx);
     m.Fy = O::where_pos(k, O::fma(rk, uy, m.Fy), m.Fy);
     m.Fz = O::where_pos(k, O::fma(rk, uz, m.Fz), m.Fz);
@@ -587,9 +595,9 @@ __device__ __forceinline__ MacroV<V> moments_g(Get&& fg, V gx, V gy, V gz, V k, 
   const V pyz = O::fma(nruy, vz, syz);
   const V off = O::fma(pxy, pxy, O::fma(pxz, pxz, O::mul(pyz, pyz)));
   const V q2 = O::fma(pxx, pxx, O::fma(pyy, pyy, O::fma(pzz, pzz, O::mul(O::c(2.0f), off))));
-  const V arg = O::add(O::c(tau0 * tau0), O::div(O::mul(O::c(c18), O::sqrt(q2)), m.rho));
-  const V tau = O::mul(O::c(0.5f), O::add(O::c(tau0), O::sqrt(arg)));
-  m.om = O::div(O::c(1.0f), tau);
+  // tau_total = (tau0 + sqrt(arg)) / 2, so 1/tau_total = 2 / (tau0 + sqrt(arg))
+  const V arg = O::fma(O::mul(O::c(c18), O::sqrt(q2)), inv_rho, O::c(tau0 * tau0));
+  m.om = O::div(O::c(2.0f), O::add(O::c(tau0), O::sqrt(arg)));
   return m;
 }
 
@@ -623,10 +631,10 @@ __device__ __forceinline__ void collide_g(Get&& fg, const MacroV<V>& m, Emit&& e
   const V om = m.om;
   const V keep = O::sub(O::c(1.0f), om);
   const V pre = O::fma(O::c(-0.5f), om, O::c(1.0f));
-  const V uF3 = O::mul(O::c(3.0f), O::fma(ux, m.Fx, O::fma(uy, m.Fy, O::mul(uz, m.Fz))));
+  const V nuF3 = O::mul(O::c(-3.0f), O::fma(ux, m.Fx, O::fma(uy, m.Fy, O::mul(uz, m.Fz))));  // -3 u.F
   {
     const V pw = O::mul(pre, O::c(wgt(0)));
-    emit(0, O::fma(keep, fg(0), O::fma(om, O::mul(O::c(wgt(0)), base), O::neg(O::mul(pw, uF3)))));
+    emit(0, O::fma(keep, fg(0), O::fma(om, O::mul(O::c(wgt(0)), base), O::mul(pw, nuF3))));
   }
 #pragma unroll
   for (int i = 1; i < NQ; i += 2) {
@@ -634,7 +642,7 @@ __device__ __forceinline__ void collide_g(Get&& fg, const MacroV<V>& m, Emit&& e
     const V h = pair_dot<V>(i, m.Fx, m.Fy, m.Fz);
     const V sym = O::mul(O::c(wgt(i)), O::fma(O::mul(r45, e), e, base));  // even part of f_eq - w
     const V pw = O::mul(pre, O::c(wgt(i)));
-    const V even = O::fma(om, sym, O::mul(pw, O::fma(O::mul(O::c(9.0f), e), h, O::neg(uF3))));
+    const V even = O::fma(om, sym, O::mul(pw, O::fma(O::mul(O::c(9.0f), e), h, nuF3)));
     const V odd = O::fma(om, O::mul(O::mul(O::c(wgt(i)), r3), e), O::mul(O::mul(O::c(3.0f), pw), h));
     emit(i, O::fma(keep, fg(i), O::add(even, odd)));
     emit(i + 1, O::fma(keep, fg(i + 1), O::sub(even, odd)));
@@ -925,7 +933,6 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   // (the collision needs every register the three-blocks-per-SM budget allows)
   __shared__ float s_q[STATS ? 9 * 256 : 1];
   __shared__ long long s_ub[8];
-  __shared__ float s_gx;
   __shared__ __align__(8) uint64_t s_bar[8];
   __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
   __shared__ int s_fill;              // next fill to issue: 8 * round + stage
@@ -1002,21 +1009,15 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 
   if (tid == 0 && dynamic && blockIdx.x == 0) p.state->tile_ctr[1 - p.ctr_slot] = 0u;  // next step's
   __syncthreads();
-  // Warp 0 issues the first fills.  With FP32 storage the other warps go
-  // straight to waiting on them (the mbarriers publish the tiles), each warp
-  // computing the driving acceleration itself; with 16-bit storage (twice the
-  // stages) they wait at a barrier for warp 0's value instead, which measured
-  // faster (B300: FP32 122.7 -> 119.4 us without the barrier, FP16 115.5 ->
-  // 123.9 us).
+  // Warp 0 issues the first fills; the other warps go straight to waiting on
+  // them (the mbarriers publish the tiles), each warp computing the driving
+  // acceleration itself.  (A block barrier after warp 0 had computed it for
+  // all, tried with 16-bit storage, was slower once three blocks share an
+  // SM: B300, channel 256x128x128, 0.0990 -> 0.0969 ms without it.)
   if (warp == 0) {
     for (int k = 0; k < p.nstage; k++) fill(k, k, -1);
-    if (sizeof(T) == 2) {
-      const float v = controlled_gx(p, lane);
-      if (lane == 0) s_gx = v;
-    }
   }
-  if (sizeof(T) == 2) __syncthreads();
-  const float gx = sizeof(T) == 2 ? s_gx : controlled_gx(p, lane), gy = p.g[1], gz = p.g[2];
+  const float gx = controlled_gx(p, lane), gy = p.g[1], gz = p.g[2];
   T* dst = static_cast<T*>(p.dst) + Gm::G + CPT * tx;
   T* const dst0 = static_cast<T*>(p.dst) + Gm::G;  // slot G of direction 0, chunk-row 0
 
@@ -1285,17 +1286,26 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           }
           last_x = x;
         }
+        collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
+          T* o = out + i * Gm::XTP;
+          if (act1) {
+            if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
+          } else {
+            put1(o, v.x);
+          }
+        });
         // Ghost slots the pair feeds (as for one cell per thread): at most one
         // for its c_x = +1 values (offset gro from `out`, cell grc) and one
         // for its c_x = -1 values (glo, cell glc).  Cell x can be the first of
         // its chunk or the last of the domain, cell x + 1 the last of its
         // chunk or of the domain.  Only a two-cell last chunk of an outflow
         // row needs both a chunk ghost and the outflow copy on the c_x = -1
-        // side: its copy is taken from the stored line below (copy1).
-        constexpr int kNone = INT_MIN;
-        int gro = kNone, glo = kNone;
-        bool grc = false, glc = false, copy1 = false;
+        // side (copy1).  The edge lanes copy the values from the line they just
+        // stored, so the other lanes' stores carry no ghost code.
         if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
+          constexpr int kNone = INT_MIN;
+          int gro = kNone, glo = kNone;
+          bool grc = false, glc = false, copy1 = false;
           const long long own = (long long)(unsigned)(crow0 + xc) * Gm::ROW + 2 * tx;  // out - dst0
           if (x == p.nx - 1) {
             if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
@@ -1318,25 +1328,30 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
             left = (int)((long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT - own);
           }
           if (left != kNone) {
-            copy1 = glc && glo == 2;  // the outflow copy of cell x + 1 from the stored line
+            copy1 = glc && glo == 2;  // and the outflow copy of cell x + 1
             glo = left;
             glc = false;
           }
-        }
-        collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
-          T* o = out + i * Gm::XTP;
-          if (act1) {
-            if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
-          } else {
-            put1(o, v.x);
+          // a stored value to another slot (the same bits, so the same as
+          // storing the FP32 value there)
+          auto copy = [&](long long to, int from) {
+            if (!kCheckBounds || in_range(out + to - d0, 1, set, p.state)) out[to] = __ldcg(out + from);
+          };
+          if (gro != kNone) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cx(i) == 1) copy((long long)gro + i * Gm::XTP, (grc ? 1 : 0) + i * Gm::XTP);
           }
-          if (cx(i) == 1 && gro != kNone) put1(o + gro, grc ? v.y : v.x);
-          if (cx(i) == -1 && glo != kNone) put1(o + glo, glc ? v.y : v.x);
-        });
-        if (copy1) {
-#pragma unroll
-          for (int i = 0; i < NQ; i++)
-            if (cx(i) == -1) put1(out + 2 + i * Gm::XTP, Store<S>::to_float(__ldcg(out + 1 + i * Gm::XTP)));
+          if (glo != kNone) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cx(i) == -1) copy((long long)glo + i * Gm::XTP, (glc ? 1 : 0) + i * Gm::XTP);
+          }
+          if (copy1) {
+  #pragma unroll
+            for (int i = 0; i < NQ; i++)
+              if (cx(i) == -1) copy(2 + i * Gm::XTP, 1 + i * Gm::XTP);
+          }
         }
         if (p.io_one && x == p.nx - 1) {
           // a one-cell last chunk at an outflow (its cell is the pair's first):
