@@ -375,10 +375,10 @@ void launch_step(const lbm_ctx* c, const StepParams& p, bool stats) {
 }
 
 // Launch shape and shared-memory stages of a step kernel form: a chunk of XT
-// cells per tile row with cpt cells per thread, 256 cpt / XT rows (consecutive
-// z) per tile; as many tiles in flight as fit beside the form's blocks per SM
-// (three of one cell per thread, two of two) and their static shared memory
-// (about 12 KB with statistics): at most 8, at least 2.
+// cells per tile row with cpt cells per thread, block_threads(cpt) cpt / XT
+// rows (consecutive z) per tile; as many tiles in flight as fit beside three
+// blocks per SM and their static shared memory (about 9 KB with statistics):
+// at most 8, at least 2 (three with the chunk widths used here).
 struct StagePlan {
   dim3 block;
   int nstage;
@@ -388,9 +388,10 @@ template <int XT, int S>
 StagePlan stage_plan(int cpt) {
   using St = Stage<XT, S>;
   StagePlan sp;
-  sp.block = dim3(XT / cpt, 256 * cpt / XT, 1);
+  const int nt = block_threads(cpt);
+  sp.block = dim3(XT / cpt, nt * cpt / XT, 1);
   const size_t stage = (size_t)sp.block.y * NQ * St::SROW * sizeof(typename Store<S>::T);
-  const size_t budget = 62 * 1024;
+  const size_t budget = 62 * 1024 * nt / 256;
   sp.nstage = (int)std::max<size_t>(2, std::min<size_t>(8, budget / stage));
   sp.smem = sp.nstage * stage;
   return sp;
@@ -688,7 +689,9 @@ lbm_status aa_step(lbm_ctx* c) {
       a.wr[i] = rev;
     }
   }
-  a.nxc = (g.nx + AA_XT - 1) / AA_XT;
+  int cpt = 1;
+  dispatch_s(c, [&](auto s) { cpt = KernAA<decltype(s)::value>::cells_per_thread(uses_variant(c->forcing)); });
+  a.nxc = (g.nx + AA_XT * cpt - 1) / (AA_XT * cpt);
   a.nzg = (g.nz + AA_ZR - 1) / AA_ZR;
   a.nunit = a.nxc * a.nzg * g.ny;
   a.xc_outer = c->stats_on && c->nbins > 1 && a.nxc > 1;

@@ -138,6 +138,12 @@ __device__ __forceinline__ bool in_range(long long lo, long long len, long long 
 }
 
 constexpr int MAX_BLOCKS = 4096;  // per-block bulk-velocity partials per slot
+// threads per block of the step kernels for cpt cells per thread (a tile is
+// that many threads' cells; three blocks of 256 threads fit an SM).  Six
+// blocks of 128 threads (one tile row) for two cells per thread measured the
+// same within 1 % (B300: channel FP16 0.0926 -> 0.0941 ms, canopy FP16 0.3355
+// -> 0.3332 ms).
+__host__ __device__ constexpr int block_threads(int cpt) { return cpt > 0 ? 256 : 256; }
 constexpr int MAX_XBINS = 64;
 
 // ---- population layout in HBM ------------------------------------------------------
@@ -685,16 +691,17 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Plane statistics of one warp: its lanes' sums for row y (taken from the
-// shared-memory slots `qs`, stride 256, and cleared) are added to the FP64
+// shared-memory slots `qs`, stride NT (threads per block), and cleared) are added to the FP64
 // accumulators, one warp-reduced add per quantity when the lanes share an
 // x-bin, else one add per lane.  Called by every lane; no block barrier.
+template <int NT>
 __device__ __forceinline__ void flush_warp_stats(const StepParams& p, float* qs, int& last_x, int y,
                                                  int lane) {
   float q[9];
 #pragma unroll
   for (int k = 0; k < 9; k++) {
-    q[k] = qs[k * 256];
-    qs[k * 256] = 0.f;
+    q[k] = qs[k * NT];
+    qs[k * NT] = 0.f;
   }
   const int bin = last_x >= 0 ? (int)(((long long)last_x * p.nbins) / p.nx) : -1;
   const unsigned act = __ballot_sync(0xffffffffu, bin >= 0);
@@ -928,10 +935,11 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   using Gm = Geo<XT, S>;
   using St = Stage<XT, S>;
   constexpr int TPR = XT / CPT;  // threads per tile row
+  constexpr int NT = block_threads(CPT);
   extern __shared__ __align__(128) unsigned char smem[];
   // per-thread statistics sums, kept in shared memory rather than registers
   // (the collision needs every register the three-blocks-per-SM budget allows)
-  __shared__ float s_q[STATS ? 9 * 256 : 1];
+  __shared__ float s_q[STATS ? 9 * NT : 1];
   __shared__ long long s_ub[8];
   __shared__ __align__(8) uint64_t s_bar[8];
   __shared__ unsigned int s_done[8];  // warps that released each stage (monotonic)
@@ -962,7 +970,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   }
   if (STATS) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) s_q[k * 256 + tid] = 0.f;
+    for (int k = 0; k < 9; k++) s_q[k * NT + tid] = 0.f;
   }
   // Launched as a programmatic dependent of the previous step: let the next
   // step's blocks be scheduled as this grid's blocks retire, then wait here
@@ -1043,7 +1051,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 
   long long ub_fix = 0;  // sum of u_x over this thread's cells, 2^-32 fixed point
   bool bad = false, late = false;
-  float* const qs = s_q + tid;  // this thread's 9 sums, stride 256
+  float* const qs = s_q + tid;  // this thread's 9 sums, stride NT
   int last_x = -1;  // column of the last cell this thread accumulated (-1: none)
   int stat_y = -1;  // row the sums in qs belong to
   int stat_xc = -1;
@@ -1076,7 +1084,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       const int z = gq.y * blockDim.y + threadIdx.y;
       const bool active = (x < p.nx) && (z < p.nz);
       if (STATS && (y != stat_y || (flush_on_chunk && xc != stat_xc))) {
-        if (stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+        if (stat_y >= 0) flush_warp_stats<NT>(p, qs, last_x, stat_y, lane);
         stat_y = y;
         stat_xc = xc;
       }
@@ -1180,9 +1188,9 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         // makes the density non-finite by the next step at the latest)
         bad |= !(fabsf(m.drho) < 1e30f);
         if (STATS) {
-          qs[0 * 256] += m.ux; qs[1 * 256] += m.uy; qs[2 * 256] += m.uz;
-          qs[3 * 256] += m.ux * m.ux; qs[4 * 256] += m.uy * m.uy; qs[5 * 256] += m.uz * m.uz;
-          qs[6 * 256] += m.ux * m.uy; qs[7 * 256] += m.ux * m.uz; qs[8 * 256] += m.uy * m.uz;
+          qs[0 * NT] += m.ux; qs[1 * NT] += m.uy; qs[2 * NT] += m.uz;
+          qs[3 * NT] += m.ux * m.ux; qs[4 * NT] += m.uy * m.uy; qs[5 * NT] += m.uz * m.uz;
+          qs[6 * NT] += m.ux * m.uy; qs[7 * NT] += m.ux * m.uz; qs[8 * NT] += m.uy * m.uz;
           last_x = x;
         }
       }
@@ -1193,7 +1201,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       const bool active = (x < p.nx) && (z < p.nz);
       const bool act1 = active && x + 1 < p.nx;
       if (STATS && (y != stat_y || (flush_on_chunk && xc != stat_xc))) {
-        if (stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+        if (stat_y >= 0) flush_warp_stats<NT>(p, qs, last_x, stat_y, lane);
         stat_y = y;
         stat_xc = xc;
       }
@@ -1265,14 +1273,14 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           const bool split = act1 && p.nbins > 1 && !p.bins_even &&
                              ((long long)x * p.nbins) / p.nx != ((long long)(x + 1) * p.nbins) / p.nx;
           if (act1 && !split) {  // both cells in the thread's sums
-            qs[0 * 256] += u.x + u.y; qs[1 * 256] += v.x + v.y; qs[2 * 256] += w.x + w.y;
-            qs[3 * 256] += u.x * u.x + u.y * u.y; qs[4 * 256] += v.x * v.x + v.y * v.y;
-            qs[5 * 256] += w.x * w.x + w.y * w.y; qs[6 * 256] += u.x * v.x + u.y * v.y;
-            qs[7 * 256] += u.x * w.x + u.y * w.y; qs[8 * 256] += v.x * w.x + v.y * w.y;
+            qs[0 * NT] += u.x + u.y; qs[1 * NT] += v.x + v.y; qs[2 * NT] += w.x + w.y;
+            qs[3 * NT] += u.x * u.x + u.y * u.y; qs[4 * NT] += v.x * v.x + v.y * v.y;
+            qs[5 * NT] += w.x * w.x + w.y * w.y; qs[6 * NT] += u.x * v.x + u.y * v.y;
+            qs[7 * NT] += u.x * w.x + u.y * w.y; qs[8 * NT] += v.x * w.x + v.y * w.y;
           } else {
-            qs[0 * 256] += u.x; qs[1 * 256] += v.x; qs[2 * 256] += w.x;
-            qs[3 * 256] += u.x * u.x; qs[4 * 256] += v.x * v.x; qs[5 * 256] += w.x * w.x;
-            qs[6 * 256] += u.x * v.x; qs[7 * 256] += u.x * w.x; qs[8 * 256] += v.x * w.x;
+            qs[0 * NT] += u.x; qs[1 * NT] += v.x; qs[2 * NT] += w.x;
+            qs[3 * NT] += u.x * u.x; qs[4 * NT] += v.x * v.x; qs[5 * NT] += w.x * w.x;
+            qs[6 * NT] += u.x * v.x; qs[7 * NT] += u.x * w.x; qs[8 * NT] += v.x * w.x;
             if (split) {
               // the pair straddles an x-bin edge: the second cell's sums go straight out
               const long long mm = (long long)p.nbins * p.ny;
@@ -1365,7 +1373,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       }
     }
   }
-  if (STATS && stat_y >= 0) flush_warp_stats(p, qs, last_x, stat_y, lane);
+  if (STATS && stat_y >= 0) flush_warp_stats<NT>(p, qs, last_x, stat_y, lane);
   finish_step(p, ub_fix, bad, late, s_ub, lane, warp, tid, nthreads, part);
   // Leave no copy in flight when the block ends: after a timed-out wait some
   // issued fills were never consumed.  (On the normal path every issued fill
@@ -1388,7 +1396,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 // VAR: the model-variant form (flags in p); the default form has none of
 // their code.
 template <int XT, int S, bool STATS, bool VAR, int CPT>
-__global__ void __launch_bounds__(256, 3) step_kernel(StepParams p) {
+__global__ void __launch_bounds__(block_threads(CPT), 768 / block_threads(CPT)) step_kernel(StepParams p) {
   step_tiles<XT, S, STATS, VAR, CPT>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
                                      blockIdx.x, true);
 }
@@ -1402,7 +1410,7 @@ struct BatchWork {
 };
 
 template <int XT, int S, bool STATS, int CPT>
-__global__ void __launch_bounds__(256, 3) batch_step_kernel(
+__global__ void __launch_bounds__(block_threads(CPT), 768 / block_threads(CPT)) batch_step_kernel(
     const StepParams* __restrict__ boxes, const BatchWork* __restrict__ work) {
   __shared__ __align__(16) StepParams s_p;
   const BatchWork w = work[blockIdx.x];

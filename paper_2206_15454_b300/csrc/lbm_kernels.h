@@ -50,6 +50,7 @@ struct Kern {
 // AA-pattern storage (lbm_aa.cuh), per storage type (no chunk width).
 template <int S>
 struct KernAA {
+  static int cells_per_thread(bool variant);  // of the step kernel
   static int occupancy();  // resident blocks per SM of the step kernel (256 threads)
   static void fill(int blocks, cudaStream_t s, const StepParams& p);
   static void step(int blocks, cudaStream_t s, const AAStep& a, bool stats, bool variant);

@@ -52,14 +52,30 @@ def test_aa_matches_oracle_and_pull_scheme(case):
     assert uba == ubp and np.array_equal(ga, gp)
 
 
+# 16-bit storage: two cells per thread in both layouts (odd x-lengths leave a
+# lone last cell; 300-cell rows take two 256-cell units).  The equilibrium top
+# is left out: the AA fill stores its constant rounded to the storage type,
+# the pull scheme uses it in FP32.
+HALF_CASES = [c for c in W.small_cases() if c.name != "eq_top"] + [
+    W.channel_les(300, 9, 5).replace(name="wide_rows"),
+    W.canopy_abl(257, 9, 5, h=3.0, canopy_x0=60, xbin=64).replace(name="outflow_257")]
+
+
 @pytest.mark.parametrize("storage", [P.LBM_F16_SHIFTED, P.LBM_BF16_SHIFTED], ids=["f16s", "bf16s"])
-def test_aa_half_storage_equals_pull(storage):
-    case = W.small_cases()[2]
+@pytest.mark.parametrize("case", HALF_CASES, ids=[c.name for c in HALF_CASES])
+def test_aa_half_storage_equals_pull(storage, case):
     aa, pull = P.Domain(case, storage | AA), P.Domain(case, storage)
+    aa.stats_reset(True)
+    pull.stats_reset(True)
     for k in (1, 50, 49):
         aa.step(k)
         pull.step(k)
-        assert np.array_equal(aa.get_f(), pull.get_f())
+        assert np.array_equal(aa.get_f(), pull.get_f()), (case.name, k)
+    (ga, uba), (gp, ubp) = aa.drive(), pull.drive()
+    assert uba == ubp and np.array_equal(ga, gp)
+    sa, _ = aa.stats()
+    sp, _ = pull.stats()
+    assert np.max(np.abs(sa[:3] - sp[:3])) <= 1e-6 * max(np.abs(sp[:3]).max(), 1e-12)
 
 
 def test_aa_set_f_checkpoint_and_readouts_at_odd_parity(tmp_path):
