@@ -463,18 +463,23 @@ void launch_macro_any(const lbm_ctx* c, const StepParams& p, float* out) {
 void launch_correction(const lbm_ctx* c, const float* th, float* X) {
   const StepParams p = make_params(c);
   const long long cols = (long long)c->grid.nx * c->grid.nz;
+  if (th) {
+    // features and network in one pass: resident blocks of four warps, each
+    // staging the weights once and taking tiles of 16 columns in turn
+    const long long tiles = (cols + 15) / 16;
+    dispatch(c, [&](auto xt, auto s) {
+      using K = Kern<decltype(xt)::value, decltype(s)::value>;
+      const long long resident = (long long)c->sm_count * K::correction_occupancy();
+      const int blocks = (int)std::max<long long>(1, std::min<long long>((tiles + 3) / 4, resident));
+      K::correction(blocks, c->stream, p, th, c->lam, c->accel());
+    });
+    return;
+  }
   const int fblocks = (int)std::max<long long>(1, std::min<long long>((cols + 255) / 256,
                                                                       (long long)c->sm_count * 16));
   dispatch(c, [&](auto xt, auto s) {
     Kern<decltype(xt)::value, decltype(s)::value>::features(fblocks, c->stream, p, X);
   });
-  if (th) {
-    const long long tiles = (cols + 15) / 16;
-    // few blocks, many rows each: every block stages the weights once
-    const int mblocks = (int)std::max<long long>(1, std::min<long long>((tiles + 3) / 4,
-                                                                        (long long)c->sm_count * 2));
-    mlp_launch_accel(mblocks, c->stream, th, X, cols, c->lam, c->accel());
-  }
 }
 
 // The feature staging buffer (nx*nz rows of 9 floats), allocated on first use.

@@ -40,6 +40,11 @@ struct Kern {
   static void macro(int blocks, cudaStream_t s, const StepParams& p, float* out);
   static void macro_d(int blocks, cudaStream_t s, const StepParams& p, double* out);
   static void features(int blocks, cudaStream_t s, const StepParams& p, float* X);
+  // The learned correction after a step: column features and network in one
+  // pass, the layer-0 acceleration into accel.
+  static void correction(int blocks, cudaStream_t s, const StepParams& p, const float* th,
+                         float lam, float2* accel);
+  static int correction_occupancy();
   // x-halo faces of a slab: pack from / unpack into population set f.
   static void halo_pack(int blocks, cudaStream_t s, const StepParams& p, const void* f, void* lo,
                         void* hi);
@@ -61,8 +66,6 @@ struct KernAA {
 };
 
 // ---- the learned correction's network (lbm_mlp.cu; kernels in lbm_mlp.cuh) ----
-void mlp_launch_accel(int blocks, cudaStream_t s, const float* th, const float* X, long long n,
-                      float lam, float2* accel);
 void mlp_launch_infer(int blocks, cudaStream_t s, const float* th, const float* X, long long n,
                       float* Y);
 void mlp_launch_train_fwd(int blocks, cudaStream_t s, const float* th, const float* X,

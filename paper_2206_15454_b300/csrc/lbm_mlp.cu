@@ -5,11 +5,6 @@
 
 namespace lbm {
 
-void mlp_launch_accel(int blocks, cudaStream_t s, const float* th, const float* X, long long n,
-                      float lam, float2* accel) {
-  mlp_accel_kernel<<<blocks, 128, 0, s>>>(th, X, n, lam, accel);
-}
-
 void mlp_launch_infer(int blocks, cudaStream_t s, const float* th, const float* X, long long n,
                       float* Y) {
   mlp_infer_kernel<<<blocks, 128, 0, s>>>(th, X, n, Y);
