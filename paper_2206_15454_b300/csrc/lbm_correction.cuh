@@ -18,7 +18,7 @@ namespace lbm {
 // values features_kernel would have written (the same FP32 arithmetic), so
 // the field equals that of the network on lbm_features' output.
 template <int XT, int S>
-__global__ void __launch_bounds__(128, 4) correction_kernel(StepParams p, const float* __restrict__ th,
+__global__ void __launch_bounds__(128, 5) correction_kernel(StepParams p, const float* __restrict__ th,
                                                             float lam, float2* __restrict__ accel) {
   __shared__ MlpSmem s;
   __shared__ __align__(16) __nv_bfloat16 xin[4][16 * 16];

@@ -1619,20 +1619,22 @@ __device__ __forceinline__ float strain_rate(const float* f, const Macro& m, flo
   const float hx = edm ? 0.5f * m.Fx / m.rho : 0.f, hy = edm ? 0.5f * m.Fy / m.rho : 0.f,
               hz = edm ? 0.5f * m.Fz / m.rho : 0.f;  // exact difference: f_eq at u - g/2
   const float ux = m.ux - hx, uy = m.uy - hy, uz = m.uz - hz;
-  const float base = m.drho - 1.5f * m.rho * (ux * ux + uy * uy + uz * uz);
-  const float r45 = 4.5f * m.rho;
-  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+  // Pi_neq = S - c_s^2 (rho - 1) I - rho u u, S the second moments of the
+  // shifted populations (the second moment of f_eq is rho c_s^2 I + rho u u)
+  float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
 #pragma unroll
   for (int i = 1; i < NQ; i += 2) {
-    const float ei = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-    const float npair = (f[i] + f[i + 1]) - 2.0f * wgt(i) * (base + r45 * ei * ei);
-    if (cx(i) != 0) pxx += npair;
-    if (cy(i) != 0) pyy += npair;
-    if (cz(i) != 0) pzz += npair;
-    pxy += (float)(cx(i) * cy(i)) * npair;
-    pxz += (float)(cx(i) * cz(i)) * npair;
-    pyz += (float)(cy(i) * cz(i)) * npair;
+    const float sp = f[i] + f[i + 1];
+    if (cx(i) != 0) sxx += sp;
+    if (cy(i) != 0) syy += sp;
+    if (cz(i) != 0) szz += sp;
+    if (cx(i) * cy(i) != 0) sxy += (float)(cx(i) * cy(i)) * sp;
+    if (cx(i) * cz(i) != 0) sxz += (float)(cx(i) * cz(i)) * sp;
+    if (cy(i) * cz(i) != 0) syz += (float)(cy(i) * cz(i)) * sp;
   }
+  const float d3 = m.drho * (1.0f / 3.0f), r = m.rho;
+  const float pxx = sxx - d3 - r * ux * ux, pyy = syy - d3 - r * uy * uy, pzz = szz - d3 - r * uz * uz;
+  const float pxy = sxy - r * ux * uy, pxz = sxz - r * ux * uz, pyz = syz - r * uy * uz;
   const float q2 = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
   const float q = sqrtf(q2);
   const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + c18 * q / (tau_rho2 ? m.rho * m.rho : m.rho)));

@@ -32,27 +32,35 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 
 // Weights staged in shared memory for the tensor-core pass: BF16, row-major
 // [out][in]; the first layer's inputs are padded to 16, the last layer's
-// outputs to 8 (padding zero).
+// outputs to 8 (padding zero).  Rows are MLP_WPAD elements longer than their
+// inputs, so the eight rows a warp's B fragments read (one per lane group)
+// fall in different banks: with rows 128 bytes apart every fragment load was
+// an 8-way bank conflict.
+constexpr int MLP_WPAD = 8;
 struct MlpSmem {
-  __nv_bfloat16 w1[64 * 16];
-  __nv_bfloat16 w2[64 * 64];
-  __nv_bfloat16 w3[64 * 64];
-  __nv_bfloat16 w4[8 * 64];
+  __nv_bfloat16 w1[64 * (16 + MLP_WPAD)];
+  __nv_bfloat16 w2[64 * (64 + MLP_WPAD)];
+  __nv_bfloat16 w3[64 * (64 + MLP_WPAD)];
+  __nv_bfloat16 w4[8 * (64 + MLP_WPAD)];
   float b1[64], b2[64], b3[64], b4[8];
   float xm[16], xinv[16], ym[4], ys[4];
 };
 
 __device__ __forceinline__ void mlp_stage(MlpSmem& s, const float* __restrict__ th) {
-  for (int k = threadIdx.x; k < 64 * 16; k += blockDim.x) {
-    const int o = k / 16, i = k % 16;
+  constexpr int R1 = 16 + MLP_WPAD, R = 64 + MLP_WPAD;  // row strides
+  for (int k = threadIdx.x; k < 64 * R1; k += blockDim.x) {
+    const int o = k / R1, i = k % R1;
     s.w1[k] = __float2bfloat16_rn(i < MLP_IN ? th[OFF_W1 + o * MLP_IN + i] : 0.f);
   }
-  for (int k = threadIdx.x; k < 64 * 64; k += blockDim.x) {
-    s.w2[k] = __float2bfloat16_rn(th[OFF_W2 + k]);
-    s.w3[k] = __float2bfloat16_rn(th[OFF_W3 + k]);
+  for (int k = threadIdx.x; k < 64 * R; k += blockDim.x) {
+    const int o = k / R, i = k % R;
+    s.w2[k] = __float2bfloat16_rn(i < 64 ? th[OFF_W2 + o * 64 + i] : 0.f);
+    s.w3[k] = __float2bfloat16_rn(i < 64 ? th[OFF_W3 + o * 64 + i] : 0.f);
   }
-  for (int k = threadIdx.x; k < 8 * 64; k += blockDim.x)
-    s.w4[k] = __float2bfloat16_rn(k < 4 * 64 ? th[OFF_W4 + k] : 0.f);
+  for (int k = threadIdx.x; k < 8 * R; k += blockDim.x) {
+    const int o = k / R, i = k % R;
+    s.w4[k] = __float2bfloat16_rn(o < 4 && i < 64 ? th[OFF_W4 + o * 64 + i] : 0.f);
+  }
   for (int k = threadIdx.x; k < 64; k += blockDim.x) {
     s.b1[k] = th[OFF_B1 + k];
     s.b2[k] = th[OFF_B2 + k];
@@ -84,7 +92,7 @@ __device__ __forceinline__ void mlp_hidden(const uint32_t (&a)[KS][4], uint32_t 
     d[1] = b[8 * j + 2 * t + 1];
     d[2] = d[0];
     d[3] = d[1];
-    const __nv_bfloat16* wr = w + (8 * j + g) * K + 2 * t;  // W[n = 8j + g][k]
+    const __nv_bfloat16* wr = w + (8 * j + g) * (K + MLP_WPAD) + 2 * t;  // W[n = 8j + g][k]
 #pragma unroll
     for (int s = 0; s < KS; s++) {
       const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 16 * s);
@@ -119,7 +127,7 @@ __device__ __forceinline__ void mlp_rows16(const MlpSmem& s, const __nv_bfloat16
   d[1] = s.b4[2 * t + 1];
   d[2] = d[0];
   d[3] = d[1];
-  const __nv_bfloat16* wr = s.w4 + g * 64 + 2 * t;
+  const __nv_bfloat16* wr = s.w4 + g * (64 + MLP_WPAD) + 2 * t;
 #pragma unroll
   for (int k = 0; k < 4; k++) {
     const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + 16 * k);
