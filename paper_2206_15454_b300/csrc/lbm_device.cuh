@@ -927,7 +927,10 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
 // CPT: cells per thread along x, 1 or 2 (16-bit storage, default model:
 // packed FP32x2 arithmetic on two adjacent cells, one 32-bit access per pair
 // where the pair is aligned); the block is (XT / CPT) x (256 CPT / XT).
-template <int XT, int S, bool STATS, bool VAR, int CPT>
+// BATCH: a work item of an ensemble (a short static run of one box, the
+// pipeline started anew for each): two choices differ from the single domain's
+// persistent blocks, see kItemBarrier and kItemInlineGhosts.
+template <int XT, int S, bool STATS, bool VAR, int CPT, bool BATCH = false>
 __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part,
                                            bool dynamic) {
   static_assert(CPT == 1 || (CPT == 2 && !VAR), "two cells per thread: default model only");
@@ -1025,6 +1028,17 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
   if (warp == 0) {
     for (int k = 0; k < p.nstage; k++) fill(k, k, -1);
   }
+  // An ensemble's work items start the pipeline about eight times as often as
+  // the persistent single-domain blocks: there the other warps wait at a
+  // barrier while warp 0 issues the first fills rather than poll beside it
+  // (B300, 64-box FP16 ensemble: 1.31 ms per step with polling and the ghost
+  // copies below, 1.02 ms with the barrier and ghosts stored with the cells).
+  constexpr bool kItemBarrier = BATCH && sizeof(T) == 2;
+  // Ensemble rows are short (a chunk edge in nearly every active warp): there
+  // the two-cell form stores the ghost slots with the cells instead of copying
+  // them from the stored line afterwards.
+  constexpr bool kItemInlineGhosts = BATCH;
+  if (kItemBarrier) __syncthreads();
   const float gx = controlled_gx(p, lane), gy = p.g[1], gz = p.g[2];
   T* dst = static_cast<T*>(p.dst) + Gm::G + CPT * tx;
   T* const dst0 = static_cast<T*>(p.dst) + Gm::G;  // slot G of direction 0, chunk-row 0
@@ -1294,71 +1308,124 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           }
           last_x = x;
         }
-        collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
-          T* o = out + i * Gm::XTP;
-          if (act1) {
-            if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
-          } else {
-            put1(o, v.x);
-          }
-        });
-        // Ghost slots the pair feeds (as for one cell per thread): at most one
-        // for its c_x = +1 values (offset gro from `out`, cell grc) and one
-        // for its c_x = -1 values (glo, cell glc).  Cell x can be the first of
-        // its chunk or the last of the domain, cell x + 1 the last of its
-        // chunk or of the domain.  Only a two-cell last chunk of an outflow
-        // row needs both a chunk ghost and the outflow copy on the c_x = -1
-        // side (copy1).  The edge lanes copy the values from the line they just
-        // stored, so the other lanes' stores carry no ghost code.
-        if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
+        if constexpr (kItemInlineGhosts) {
+          // Ghost slots the pair feeds, stored with the cells: at most one for
+          // its c_x = +1 values (offset gro from `out`, cell grc) and one for
+          // its c_x = -1 values (glo, cell glc); a two-cell last chunk of an
+          // outflow row takes its outflow copy from the stored line (copy1).
           constexpr int kNone = INT_MIN;
           int gro = kNone, glo = kNone;
           bool grc = false, glc = false, copy1 = false;
-          const long long own = (long long)(unsigned)(crow0 + xc) * Gm::ROW + 2 * tx;  // out - dst0
-          if (x == p.nx - 1) {
-            if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
-            else if (p.x_io == X_INOUT) glo = 1;
-          } else if (act1 && x + 1 == p.nx - 1) {
-            grc = glc = true;
-            if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
-            else if (p.x_io == X_INOUT) glo = 2;
-          } else if (act1 && tx == TPR - 1) {
-            grc = true;
-            gro = (int)((long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1 - own);
-          }
-          int left = kNone;
-          if (x == 0) {
-            if (p.x_io == X_PERIODIC) {
-              const int xl = p.nxc - 1;
-              left = (int)((long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT) - own);
+          if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
+            const long long own = (long long)(unsigned)(crow0 + xc) * Gm::ROW + 2 * tx;  // out - dst0
+            if (x == p.nx - 1) {
+              if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
+              else if (p.x_io == X_INOUT) glo = 1;
+            } else if (act1 && x + 1 == p.nx - 1) {
+              grc = glc = true;
+              if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
+              else if (p.x_io == X_INOUT) glo = 2;
+            } else if (act1 && tx == TPR - 1) {
+              grc = true;
+              gro = (int)((long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1 - own);
             }
-          } else if (tx == 0) {
-            left = (int)((long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT - own);
+            int left = kNone;
+            if (x == 0) {
+              if (p.x_io == X_PERIODIC) {
+                const int xl = p.nxc - 1;
+                left = (int)((long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT) - own);
+              }
+            } else if (tx == 0) {
+              left = (int)((long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT - own);
+            }
+            if (left != kNone) {
+              copy1 = glc && glo == 2;
+              glo = left;
+              glc = false;
+            }
           }
-          if (left != kNone) {
-            copy1 = glc && glo == 2;  // and the outflow copy of cell x + 1
-            glo = left;
-            glc = false;
-          }
-          // a stored value to another slot (the same bits, so the same as
-          // storing the FP32 value there)
-          auto copy = [&](long long to, int from) {
-            if (!kCheckBounds || in_range(out + to - d0, 1, set, p.state)) out[to] = __ldcg(out + from);
-          };
-          if (gro != kNone) {
-  #pragma unroll
-            for (int i = 0; i < NQ; i++)
-              if (cx(i) == 1) copy((long long)gro + i * Gm::XTP, (grc ? 1 : 0) + i * Gm::XTP);
-          }
-          if (glo != kNone) {
-  #pragma unroll
-            for (int i = 0; i < NQ; i++)
-              if (cx(i) == -1) copy((long long)glo + i * Gm::XTP, (glc ? 1 : 0) + i * Gm::XTP);
-          }
+          collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
+            T* o = out + i * Gm::XTP;
+            if (act1) {
+              if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
+            } else {
+              put1(o, v.x);
+            }
+            if (cx(i) == 1 && gro != kNone) put1(o + gro, grc ? v.y : v.x);
+            if (cx(i) == -1 && glo != kNone) put1(o + glo, glc ? v.y : v.x);
+          });
           if (copy1) {
   #pragma unroll
             for (int i = 0; i < NQ; i++)
-              if (cx(i) == -1) copy(2 + i * Gm::XTP, 1 + i * Gm::XTP);
+              if (cx(i) == -1) put1(out + 2 + i * Gm::XTP, Store<S>::to_float(__ldcg(out + 1 + i * Gm::XTP)));
+          }
+        } else {
+          collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
+            T* o = out + i * Gm::XTP;
+            if (act1) {
+              if (!kCheckBounds || in_range(o - d0, 2, set, p.state)) Store<S>::st2(o, v);
+            } else {
+              put1(o, v.x);
+            }
+          });
+          // Ghost slots the pair feeds (as for one cell per thread): at most one
+          // for its c_x = +1 values (offset gro from `out`, cell grc) and one
+          // for its c_x = -1 values (glo, cell glc).  Cell x can be the first of
+          // its chunk or the last of the domain, cell x + 1 the last of its
+          // chunk or of the domain.  Only a two-cell last chunk of an outflow
+          // row needs both a chunk ghost and the outflow copy on the c_x = -1
+          // side (copy1).  The edge lanes copy the values from the line they just
+          // stored, so the other lanes' stores carry no ghost code.
+          if (tx == 0 || tx == TPR - 1 || x + 1 >= p.nx - 1) {
+            constexpr int kNone = INT_MIN;
+            int gro = kNone, glo = kNone;
+            bool grc = false, glc = false, copy1 = false;
+            const long long own = (long long)(unsigned)(crow0 + xc) * Gm::ROW + 2 * tx;  // out - dst0
+            if (x == p.nx - 1) {
+              if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
+              else if (p.x_io == X_INOUT) glo = 1;
+            } else if (act1 && x + 1 == p.nx - 1) {
+              grc = glc = true;
+              if (p.x_io == X_PERIODIC) gro = (int)((long long)(unsigned)crow0 * Gm::ROW - 1 - own);
+              else if (p.x_io == X_INOUT) glo = 2;
+            } else if (act1 && tx == TPR - 1) {
+              grc = true;
+              gro = (int)((long long)(unsigned)(crow0 + xc + 1) * Gm::ROW - 1 - own);
+            }
+            int left = kNone;
+            if (x == 0) {
+              if (p.x_io == X_PERIODIC) {
+                const int xl = p.nxc - 1;
+                left = (int)((long long)(unsigned)(crow0 + xl) * Gm::ROW + (p.nx - xl * XT) - own);
+              }
+            } else if (tx == 0) {
+              left = (int)((long long)(unsigned)(crow0 + xc - 1) * Gm::ROW + XT - own);
+            }
+            if (left != kNone) {
+              copy1 = glc && glo == 2;  // and the outflow copy of cell x + 1
+              glo = left;
+              glc = false;
+            }
+            // a stored value to another slot (the same bits, so the same as
+            // storing the FP32 value there)
+            auto copy = [&](long long to, int from) {
+              if (!kCheckBounds || in_range(out + to - d0, 1, set, p.state)) out[to] = __ldcg(out + from);
+            };
+            if (gro != kNone) {
+    #pragma unroll
+              for (int i = 0; i < NQ; i++)
+                if (cx(i) == 1) copy((long long)gro + i * Gm::XTP, (grc ? 1 : 0) + i * Gm::XTP);
+            }
+            if (glo != kNone) {
+    #pragma unroll
+              for (int i = 0; i < NQ; i++)
+                if (cx(i) == -1) copy((long long)glo + i * Gm::XTP, (glc ? 1 : 0) + i * Gm::XTP);
+            }
+            if (copy1) {
+    #pragma unroll
+              for (int i = 0; i < NQ; i++)
+                if (cx(i) == -1) copy(2 + i * Gm::XTP, 1 + i * Gm::XTP);
+            }
           }
         }
         if (p.io_one && x == p.nx - 1) {
@@ -1423,7 +1490,7 @@ __global__ void __launch_bounds__(block_threads(CPT), 768 / block_threads(CPT)) 
       dst[k] = src[k];
   }
   __syncthreads();
-  step_tiles<XT, S, STATS, false, CPT>(s_p, w.t0, w.ntile, -1, false);
+  step_tiles<XT, S, STATS, false, CPT, true>(s_p, w.t0, w.ntile, -1, false);
 }
 
 // ---- ghost slots from the cells (after init, set_f) ----------------------------------
