@@ -132,8 +132,7 @@ __global__ void aa_fill_kernel(StepParams p) {
 struct AAStep {
   StepParams p;
   long long rd[NQ], wr[NQ];
-  // units: AA_XT threads' cells (128 or, two per thread, 256) in x x 2 z-rows
-  // at one y, numbered (y, z-group, x-chunk),
+  // units: 128 x-cells x 2 z-rows at one y, numbered (y, z-group, x-chunk),
   // or with x-binned statistics over several chunks (y, x-chunk, z-group), so
   // consecutive units of a block share their x-bins and flush less often
   int nunit, nxc, nzg, xc_outer;
@@ -141,17 +140,13 @@ struct AAStep {
 
 constexpr int AA_XT = 128, AA_ZR = 2;
 
-// One AA step (B or A, by the offsets): block b takes the units
-// [b U / G, (b + 1) U / G); CPT cells per thread (two with 16-bit storage and
-// the default model: the populations of cells x, x + 1 as packed words, as in
-// the pull kernel's two-cell form; a unit is then 256 x-cells wide); plane
-// statistics kept in registers while the unit's row and x-bin stay the same.
-// KIND (two cells per thread only): 0 step B, 1 step A; -1 either, from the
-// offsets alone (one cell per thread).
-template <int S, bool STATS, bool VAR, int CPT, int KIND>
-__global__ void __launch_bounds__(AA_XT * AA_ZR, CPT == 2 ? 2 : 3) aa_step_kernel(AAStep a) {
-  static_assert(CPT == 1 || (CPT == 2 && S != 0 && !VAR), "two cells per thread: 16-bit storage, default model");
-  static_assert((CPT == 1) == (KIND < 0), "the two-cell form is compiled per step kind");
+// One AA step (B or A, by the offsets) of the model-variant form (the default
+// model steps the AA layout on the pull scheme's tile pipeline, step_kernel
+// with AK >= 0): block b takes the units [b U / G, (b + 1) U / G); one
+// thread per cell; plane statistics kept in registers while the unit's row
+// and x-bin stay the same.
+template <int S, bool STATS, bool VAR>
+__global__ void __launch_bounds__(AA_XT * AA_ZR, 3) aa_step_kernel(AAStep a) {
   using T = typename Store<S>::T;
   const StepParams& p = a.p;
   T* const f = static_cast<T*>(p.dst);
@@ -178,17 +173,7 @@ __global__ void __launch_bounds__(AA_XT * AA_ZR, CPT == 2 ? 2 : 3) aa_step_kerne
   const float gx = s_gx, gy = p.g[1], gz = p.g[2];
   const long long u0 = (long long)blockIdx.x * a.nunit / gridDim.x;
   const long long u1 = (long long)(blockIdx.x + 1) * a.nunit / gridDim.x;
-  // the nine sums of this thread: registers (one cell per thread) or, where
-  // the two-cell collision needs every register, shared memory (stride 256)
-  constexpr bool kSmemQ = STATS && CPT == 2;
-  __shared__ float s_q[kSmemQ ? 9 * AA_XT * AA_ZR : 1];
-  float qr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float* const qs = s_q + (ty * AA_XT + tx);
-  if (kSmemQ) {
-#pragma unroll
-    for (int k = 0; k < 9; k++) qs[k * AA_XT * AA_ZR] = 0.f;
-  }
-  auto q = [&](int k) -> float& { return kSmemQ ? qs[k * AA_XT * AA_ZR] : qr[k]; };
+  float q[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int qy = -1, qbin = -1;  // row and x-bin the sums belong to
   long long ub_fix = 0;
   bool bad = false;
@@ -201,16 +186,16 @@ __global__ void __launch_bounds__(AA_XT * AA_ZR, CPT == 2 ? 2 : 3) aa_step_kerne
         const int yy = __shfl_sync(0xffffffffu, qy, __ffs(act) - 1);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-          const float v = warp_sum(q(k));
+          const float v = warp_sum(q[k]);
           if (lane == 0) atomicAdd(p.stats + k * m + (long long)b0 * p.ny + yy, (double)v);
         }
       } else if (qbin >= 0) {
 #pragma unroll
-        for (int k = 0; k < 9; k++) atomicAdd(p.stats + k * m + (long long)qbin * p.ny + qy, (double)q(k));
+        for (int k = 0; k < 9; k++) atomicAdd(p.stats + k * m + (long long)qbin * p.ny + qy, (double)q[k]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < 9; k++) q(k) = 0.f;
+    for (int k = 0; k < 9; k++) q[k] = 0.f;
     qbin = -1;
   };
   for (long long u = u0; u < u1; u++) {
@@ -226,85 +211,12 @@ __global__ void __launch_bounds__(AA_XT * AA_ZR, CPT == 2 ? 2 : 3) aa_step_kerne
       zg = (int)(r % a.nzg);
       y = (int)(r / a.nzg);
     }
-    const int x = (xc * AA_XT + tx) * CPT, z = zg * AA_ZR + ty;
+    const int x = xc * AA_XT + tx, z = zg * AA_ZR + ty;
     const bool active = x < p.nx && z < p.nz;
     const int bin = active ? (int)(((long long)x * p.nbins) / p.nx) : -1;
     if (STATS && (y != qy || __any_sync(0xffffffffu, qbin >= 0 && bin != qbin))) {
       flush();
       qy = y;
-    }
-    if constexpr (CPT == 2) {
-      if (!active) continue;
-      // cells x and x + 1: in step A every read and write is an aligned pair;
-      // in step B the ten directions with c_x != 0 read and write a pair one
-      // cell to the side (two 16-bit accesses); the second cell's element is
-      // touched only where that cell exists
-      const bool act1 = x + 1 < p.nx;
-      constexpr bool shifted = KIND == 0;
-      const long long c0 = aa_index(p, 0, x, y, z);
-      T* const cell = f + c0;
-      const unsigned short* const ch = reinterpret_cast<const unsigned short*>(cell);
-      uint32_t raw[NQ] = {};
-#pragma unroll
-      for (int i = 0; i < NQ; i++) {  // plain loads: in place
-        const long long o = a.rd[i];
-        if (kCheckBounds && !in_range(c0 + o, act1 ? 2 : 1, p.aa_elems, p.state)) continue;
-        if (cx(i) != 0 && shifted) raw[i] = __byte_perm(ch[o], act1 ? ch[o + 1] : 0u, 0x5410);
-        else raw[i] = act1 ? *reinterpret_cast<const uint32_t*>(ch + o) : (uint32_t)ch[o];
-      }
-      const float2 kd = make_float2(drag_factor(p, x, y), drag_factor(p, x + 1, y));
-      const MacroV<float2> m = moments_g<float2>(
-          [&](int i) { return Store<S>::unpack2(raw[i]); }, make_float2(gx, gx), make_float2(gy, gy),
-          make_float2(gz, gz), kd, kd.x > 0.f || kd.y > 0.f, p.tau0, p.c18);
-      auto put1 = [&](long long o, float v) {
-        if (!kCheckBounds || in_range(c0 + o, 1, p.aa_elems, p.state)) Store<S>::st(cell + o, v);
-      };
-      collide_g<float2>([&](int i) { return Store<S>::unpack2_again(raw[i]); }, m, [&](int i, float2 v) {
-        const long long o = a.wr[i];
-        if (cx(i) != 0 && shifted) {
-          put1(o, v.x);
-          if (act1) put1(o + 1, v.y);
-        } else if (act1) {
-          if (!kCheckBounds || in_range(c0 + o, 2, p.aa_elems, p.state)) Store<S>::st2(cell + o, v);
-        } else {
-          put1(o, v.x);
-        }
-      });
-      ub_fix += __float2ll_rn(m.ux.x * 4294967296.0f);
-      bad |= !(fabsf(m.drho.x) < 1e30f);
-      if (act1) {
-        ub_fix += __float2ll_rn(m.ux.y * 4294967296.0f);
-        bad |= !(fabsf(m.drho.y) < 1e30f);
-      }
-      if (STATS) {
-        const float2 u = m.ux, v = m.uy, w = m.uz;
-        const bool split = act1 && p.nbins > 1 && !p.bins_even &&
-                           ((long long)(x + 1) * p.nbins) / p.nx != bin;
-        if (act1 && !split) {  // both cells, in the order of one cell per thread
-          q(0) += u.x; q(1) += v.x; q(2) += w.x;
-          q(3) += u.x * u.x; q(4) += v.x * v.x; q(5) += w.x * w.x;
-          q(6) += u.x * v.x; q(7) += u.x * w.x; q(8) += v.x * w.x;
-          q(0) += u.y; q(1) += v.y; q(2) += w.y;
-          q(3) += u.y * u.y; q(4) += v.y * v.y; q(5) += w.y * w.y;
-          q(6) += u.y * v.y; q(7) += u.y * w.y; q(8) += v.y * w.y;
-        } else {
-          q(0) += u.x; q(1) += v.x; q(2) += w.x;
-          q(3) += u.x * u.x; q(4) += v.x * v.x; q(5) += w.x * w.x;
-          q(6) += u.x * v.x; q(7) += u.x * w.x; q(8) += v.x * w.x;
-        }
-        if (split) {
-          // the pair straddles an x-bin edge: the second cell's sums go straight out
-          const long long mm = (long long)p.nbins * p.ny;
-          double* acc = p.stats + ((long long)(x + 1) * p.nbins) / p.nx * p.ny + y;
-          atomicAdd(acc + 0 * mm, (double)u.y); atomicAdd(acc + 1 * mm, (double)v.y);
-          atomicAdd(acc + 2 * mm, (double)w.y); atomicAdd(acc + 3 * mm, (double)(u.y * u.y));
-          atomicAdd(acc + 4 * mm, (double)(v.y * v.y)); atomicAdd(acc + 5 * mm, (double)(w.y * w.y));
-          atomicAdd(acc + 6 * mm, (double)(u.y * v.y)); atomicAdd(acc + 7 * mm, (double)(u.y * w.y));
-          atomicAdd(acc + 8 * mm, (double)(v.y * w.y));
-        }
-        qbin = bin;
-      }
-      continue;
     }
     if (active) {
       const long long c0 = aa_index(p, 0, x, y, z);
@@ -331,9 +243,9 @@ __global__ void __launch_bounds__(AA_XT * AA_ZR, CPT == 2 ? 2 : 3) aa_step_kerne
       ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
       bad |= !(fabsf(m.drho) < 1e30f);
       if (STATS) {
-        q(0) += m.ux; q(1) += m.uy; q(2) += m.uz;
-        q(3) += m.ux * m.ux; q(4) += m.uy * m.uy; q(5) += m.uz * m.uz;
-        q(6) += m.ux * m.uy; q(7) += m.ux * m.uz; q(8) += m.uy * m.uz;
+        q[0] += m.ux; q[1] += m.uy; q[2] += m.uz;
+        q[3] += m.ux * m.ux; q[4] += m.uy * m.uy; q[5] += m.uz * m.uz;
+        q[6] += m.ux * m.uy; q[7] += m.ux * m.uz; q[8] += m.uy * m.uz;
         qbin = bin;
       }
     }
@@ -400,8 +312,10 @@ __global__ void aa_mass_partial_kernel(StepParams p, double* partial) {
 template <int S, class OutT>
 __global__ void aa_macro_kernel(StepParams p, OutT* out) {
   const long long n = (long long)p.nx * p.ny * p.nz;
-  float gx = p.g[0];
-  if (p.ctrl && p.have_prev)
+  // the driving acceleration the next step uses: from the one exact sum of
+  // the one-cell AA kernel, or from the tile pipeline's per-block partials
+  float gx = p.aa_ub_sum ? p.g[0] : controlled_gx(p, threadIdx.x & 31);
+  if (p.aa_ub_sum && p.ctrl && p.have_prev)
     gx = (float)(p.g0x + p.gain * (p.u_target - (double)p.ub_part[p.slot_read] *
                                                     (1.0 / 4294967296.0) * p.inv_cells));
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;

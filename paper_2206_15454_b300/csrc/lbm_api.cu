@@ -124,6 +124,7 @@ struct lbm_ctx {
   lbm_grid grid;
   int storage = 0, nbins = 1;   // element type (lbm_storage without flags)
   bool aa = false;              // AA-pattern layout: one population set
+  bool aa_tma = false;          // ... stepped by the pull scheme's tile pipeline (default model)
   AAShape ash{};
   double tau0 = 0, cs = 0;
   lbm_forcing forcing;
@@ -323,11 +324,21 @@ StepParams make_params(const lbm_ctx* c) {
   p.aa_lead = c->ash.lead;
   p.aa_elems = c->aa ? c->ash.elems : 0;
   p.aa_parity = (int)(c->steps & 1);
-  if (c->aa) {
-    // the bulk-velocity sums rotate through three slots (written, read,
-    // cleared for the next step)
+  p.aa_ub_sum = c->aa && !c->aa_tma;
+  if (p.aa_ub_sum) {
+    // the one-cell AA kernel's bulk-velocity sums rotate through three slots
+    // (written, read, cleared for the next step)
     p.slot_write = (int)(c->steps % 3);
     p.slot_read = (int)((c->steps + 2) % 3);
+  }
+  if (c->aa) {
+    // write offsets of the step's kind from the cell's slot of direction 0:
+    // step B (from the swapped layout) slot i at x + c_i, step A slot opp(i)
+    const long long ys = c->ash.pitch, zs = (g.ny + 2) * ys, qs = (g.nz + 2) * zs;
+    for (int i = 0; i < NQ; i++) {
+      const long long shift = (long long)cz(i) * zs + (long long)cy(i) * ys + cx(i);
+      p.aa_wr[i] = p.aa_parity == 0 ? (long long)i * qs + shift : (long long)opp(i) * qs;
+    }
   }
   p.state = c->state();
   if (c->aa) {
@@ -403,6 +414,7 @@ void plan_stages(lbm_ctx* c) {
   const StagePlan def = stage_plan<XT, S>(Kern<XT, S>::cells_per_thread(false));
   const StagePlan vf = stage_plan<XT, S>(Kern<XT, S>::cells_per_thread(true));
   Kern<XT, S>::configure(def.smem, vf.smem);  // per form: the same for every context
+  Kern<XT, S>::aa_configure(def.smem);
   const StagePlan& own = var ? vf : def;
   c->block = own.block;
   c->nstage = own.nstage;
@@ -605,7 +617,13 @@ lbm_status create_ctx(const lbm_grid* grid, double tau0, double cs, const double
   }
 
   // launch shape and stages (plan_stages): per chunk width, storage and model form
-  if (c->aa) {
+  c->aa_tma = c->aa && !uses_variant(c->forcing);
+  if (c->aa_tma) {
+    dispatch(c, [&](auto xt, auto s) {
+      plan_stages<decltype(xt)::value, decltype(s)::value>(c);
+      c->blocks_per_sm = Kern<decltype(xt)::value, decltype(s)::value>::aa_occupancy(c->block, c->stage_smem);
+    });
+  } else if (c->aa) {
     dispatch_s(c, [&](auto s) { c->blocks_per_sm = KernAA<decltype(s)::value>::occupancy(); });
   } else {
     dispatch(c, [&](auto xt, auto s) {
@@ -694,13 +712,25 @@ lbm_status aa_step(lbm_ctx* c) {
       a.wr[i] = rev;
     }
   }
-  int cpt = 1;
-  dispatch_s(c, [&](auto s) { cpt = KernAA<decltype(s)::value>::cells_per_thread(uses_variant(c->forcing)); });
-  a.nxc = (g.nx + AA_XT * cpt - 1) / (AA_XT * cpt);
+  a.nxc = (g.nx + AA_XT - 1) / AA_XT;
   a.nzg = (g.nz + AA_ZR - 1) / AA_ZR;
   a.nunit = a.nxc * a.nzg * g.ny;
   a.xc_outer = c->stats_on && c->nbins > 1 && a.nxc > 1;
   const int grid = (int)std::max<long long>(1, std::min<long long>(a.nunit, (long long)c->sm_count * c->blocks_per_sm));
+  if (c->aa_tma) {
+    // the boundary fill, then the step on the tile pipeline (both
+    // programmatic dependents of the kernel before them)
+    dispatch(c, [&](auto xt, auto s) {
+      KernAA<decltype(s)::value>::fill(fblocks, c->stream, p);
+      Kern<decltype(xt)::value, decltype(s)::value>::aa_step(dim3(step_grid(c)), c->block, c->stage_smem,
+                                                             c->stream, p, c->stats_on);
+    });
+    CK(c, cudaGetLastError());
+    c->last_grid = step_grid(c);
+    c->steps++;
+    if (c->stats_on) c->stats_samples++;
+    return LBM_OK;
+  }
   dispatch_s(c, [&](auto s) {
     KernAA<decltype(s)::value>::fill(fblocks, c->stream, p);
     KernAA<decltype(s)::value>::step(grid, c->stream, a, c->stats_on, uses_variant(c->forcing));
@@ -983,7 +1013,7 @@ lbm_status lbm_drive(lbm_ctx* c, double g[3], double* u_bulk) {
   lbm_status s = check_device(c);
   if (s != LBM_OK) return s;
   double ub = 0.0;
-  if (c->steps > 0 && c->aa) {  // one exact sum per step, three slots in rotation
+  if (c->steps > 0 && c->aa && !c->aa_tma) {  // one exact sum per step, three slots in rotation
     long long sum = 0;
     CK(c, cudaMemcpy(&sum, c->ub_part() + (size_t)((c->steps + 2) % 3), sizeof(long long),
                      cudaMemcpyDeviceToHost));

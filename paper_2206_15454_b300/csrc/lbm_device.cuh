@@ -222,6 +222,8 @@ struct StepParams {
   // after an even number of steps; 1 streamed)
   long long aa_pitch, aa_lead, aa_elems;  // aa_elems: elements of the set (checked builds)
   int aa_parity;
+  long long aa_wr[NQ];  // the step's write offsets of direction i from the cell's slot of direction 0
+  int aa_ub_sum;        // the bulk-velocity sum is one exact sum per step in three slots (one-cell AA kernel)
 };
 
 // x boundary modes of StepParams::x_io
@@ -860,7 +862,14 @@ struct Stage {
 // Producer: the lanes of one warp issue the bulk copies of tile t into a
 // stage: per tile row and direction, the chunk's cells of the source row plus
 // the ghost slot on the side its c_x streams from (16 bytes on that side).
-template <int XT, int S>
+// AK >= 0: the AA-pattern layout (one set, rows of aa_pitch elements in
+// planes [q][z + 1][y + 1], 128-byte aligned; a spare line before the first
+// and after the last row).  Step B (AK = 0) stages, per direction i, the
+// row of slot opp(i) at (y - c_y, z - c_z) shifted by -c_x with the 16-byte
+// block on the side c_x streams from, as the pull scheme; step A (AK = 1)
+// the row of slot i at (y, z) itself.  The boundary fill before the step has
+// written every slot these rows hold outside the domain.
+template <int XT, int S, int AK = -1>
 __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& g,
                                            unsigned char* stage, uint64_t* bar, int lane) {
   using T = typename Store<S>::T;
@@ -872,6 +881,34 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
   const int nrows = min(ry, p.nz - g.zg * ry);
   const int n = min(XT, p.nx - g.xc * XT);
   const int nal = (n + H - 1) / H * H;  // cells rounded up to 16 bytes (stays in the row)
+  if constexpr (AK >= 0) {
+    uint32_t per_row = 0;
+    for (int i = 0; i < NQ; i++) per_row += (uint32_t)(nal + (AK == 0 && cx(i) != 0 ? H : 0)) * sizeof(T);
+    if (lane == 0) mbar_expect_tx(bar, per_row * (uint32_t)nrows);
+    __syncwarp();
+    const T* set = static_cast<const T*>(p.src);
+    const int x0 = g.xc * XT;
+    for (int k = lane; k < nrows * NQ; k += 32) {
+      const int r = k / NQ, i = k - r * NQ;
+      const int z = g.zg * ry + r;
+      const int q = AK == 0 ? opp(i) : i;
+      const int ys = AK == 0 ? g.y - unpack_comp(kCY, i) : g.y;
+      const int zs = AK == 0 ? z - unpack_comp(kCZ, i) : z;
+      const int dxi = AK == 0 ? unpack_comp(kCX, i) : 0;
+      const long long row = p.aa_lead + (((long long)q * (p.nz + 2) + (zs + 1)) * (p.ny + 2) + (ys + 1)) * p.aa_pitch;
+      const T* src = set + row + x0;
+      T* dst = reinterpret_cast<T*>(stage) + (r * NQ + i) * St::SROW + H;
+      const int lo = dxi == 1 ? -H : 0, len = nal + (dxi != 0 ? H : 0);
+      if (kCheckBounds) {
+        const long long dofs = (dst + lo) - reinterpret_cast<T*>(stage);
+        if (!in_range(row + x0 + lo, len, p.aa_elems, p.state) ||
+            !in_range(dofs, len, (long long)ry * NQ * St::SROW, p.state))
+          continue;
+      }
+      bulk_g2s(dst + lo, src + lo, (uint32_t)len * sizeof(T), bar);
+    }
+    return;
+  }
   const bool eq_top_row = p.y_walls && p.top == 3 && g.y == p.ny - 1;
   // bytes per tile row: 19 rows of nal cells, the 10 with c_x != 0 with their
   // 16-byte ghost block (also for bounce-back rows, where it is not read);
@@ -930,10 +967,11 @@ __device__ __forceinline__ void issue_tile(const StepParams& p, const TileGeom& 
 // BATCH: a work item of an ensemble (a short static run of one box, the
 // pipeline started anew for each): two choices differ from the single domain's
 // persistent blocks, see kItemBarrier and kItemInlineGhosts.
-template <int XT, int S, bool STATS, bool VAR, int CPT, bool BATCH = false>
+template <int XT, int S, bool STATS, bool VAR, int CPT, bool BATCH = false, int AK = -1>
 __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, int ntile, int part,
                                            bool dynamic) {
   static_assert(CPT == 1 || (CPT == 2 && !VAR), "two cells per thread: default model only");
+  static_assert(AK < 0 || (!VAR && !BATCH), "AA-pattern tiles: default model, one domain");
   using T = typename Store<S>::T;
   using Gm = Geo<XT, S>;
   using St = Stage<XT, S>;
@@ -1015,7 +1053,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
     g.y = __shfl_sync(0xffffffffu, g.y, 0);
     // (a withheld fill neither arrives nor copies: its stage's wait can only run out)
     if (g.y >= 0 && !(j == p.withhold && blockIdx.x == 0))
-      issue_tile<XT, S>(p, g, smem + rs * stage_bytes, &s_bar[rs], lane);
+      issue_tile<XT, S, AK>(p, g, smem + rs * stage_bytes, &s_bar[rs], lane);
   };
 
   if (tid == 0 && dynamic && blockIdx.x == 0) p.state->tile_ctr[1 - p.ctr_slot] = 0u;  // next step's
@@ -1113,8 +1151,8 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         // equilibrium top (constant) differ, on the five directions entering
         // through the wall
   #pragma unroll
-        for (int i = 0; i < NQ; i++) f[i] = Store<S>::to_float(sm[i * St::SROW - cx(i)]);
-        if (p.y_walls) {
+        for (int i = 0; i < NQ; i++) f[i] = Store<S>::to_float(sm[i * St::SROW - (AK == 1 ? 0 : cx(i))]);
+        if (AK < 0 && p.y_walls) {
           if (y == 0) {
   #pragma unroll
             for (int i = 0; i < NQ; i++)
@@ -1143,7 +1181,23 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       // release the stage: the moments consumed every staged value of this warp
       __syncwarp();
       if (lane == 0) atomicAdd(&s_done[st], 1u);
-      if (active) {
+      if (AK >= 0 && active) {
+        // AA-pattern layout: direction i goes to the slot of the step's kind at
+        // offset aa_wr[i] from the cell's slot of direction 0; no ghost slots
+        const long long c0 = p.aa_lead + (((long long)(z + 1)) * (p.ny + 2) + (y + 1)) * p.aa_pitch + x;
+        T* const cell = static_cast<T*>(p.dst) + c0;
+        collide_v<float>(f, mv, [&](int i, float v) {
+          if (!kCheckBounds || in_range(c0 + p.aa_wr[i], 1, p.aa_elems, p.state)) Store<S>::st(cell + p.aa_wr[i], v);
+        });
+        ub_fix += __float2ll_rn(m.ux * 4294967296.0f);
+        bad |= !(fabsf(m.drho) < 1e30f);
+        if (STATS) {
+          qs[0 * NT] += m.ux; qs[1 * NT] += m.uy; qs[2 * NT] += m.uz;
+          qs[3 * NT] += m.ux * m.ux; qs[4 * NT] += m.uy * m.uy; qs[5 * NT] += m.uz * m.uz;
+          qs[6 * NT] += m.ux * m.uy; qs[7 * NT] += m.ux * m.uz; qs[8 * NT] += m.uy * m.uz;
+          last_x = x;
+        }
+      } else if (active) {
         const int crow0 = (y * p.nz + z) * p.nxc;  // chunk-row of chunk 0 of this row
         T* out = dst + (long long)(unsigned)(crow0 + xc) * Gm::ROW;
         // ghost slots this cell feeds (edge lanes only): its c_x = +1 values to
@@ -1225,7 +1279,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
       // again by the collision: 19 registers instead of 38
       uint32_t raw[NQ] = {};
       MacroV<float2> m;
-      const bool eqtop = p.y_walls && p.top == 3 && y == p.ny - 1;
+      const bool eqtop = AK < 0 && p.y_walls && p.top == 3 && y == p.ny - 1;
       auto f_at = [&](int i, bool again) -> float2 {
         if (cy(i) == -1 && eqtop) return make_float2(p.feq_top[i], p.feq_top[i]);
         return again ? Store<S>::unpack2_again(raw[i]) : Store<S>::unpack2(raw[i]);
@@ -1239,10 +1293,10 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
         // free-slip top, the staged row that is already the mirrored one
   #pragma unroll
         for (int i = 0; i < NQ; i++) {
-          if (cx(i) == 0) raw[i] = *reinterpret_cast<const uint32_t*>(sm + i * St::SROW);
+          if (cx(i) == 0 || AK == 1) raw[i] = *reinterpret_cast<const uint32_t*>(sm + i * St::SROW);
           else raw[i] = __byte_perm(sh[i * St::SROW - cx(i)], sh[i * St::SROW + 1 - cx(i)], 0x5410);
         }
-        if (p.y_walls) {
+        if (AK < 0 && p.y_walls) {
           if (y == 0) {
   #pragma unroll
             for (int i = 0; i < NQ; i++)
@@ -1308,7 +1362,29 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
           }
           last_x = x;
         }
-        if constexpr (kItemInlineGhosts) {
+        if constexpr (AK >= 0) {
+          // AA-pattern layout: cells x, x + 1 to the slots of the step's kind
+          // (offsets aa_wr from the cell's slot of direction 0): step A and the
+          // c_x = 0 directions of step B as aligned pairs, the other directions
+          // of step B one cell to the side as two 16-bit stores; the second
+          // cell's element only where that cell exists; no ghost slots
+          const long long c0 = p.aa_lead + (((long long)(z + 1)) * (p.ny + 2) + (y + 1)) * p.aa_pitch + x;
+          T* const cell = static_cast<T*>(p.dst) + c0;
+          auto put_aa = [&](long long o, float v) {
+            if (!kCheckBounds || in_range(c0 + o, 1, p.aa_elems, p.state)) Store<S>::st(cell + o, v);
+          };
+          collide_g<float2>([&](int i) { return f_at(i, true); }, m, [&](int i, float2 v) {
+            const long long o = p.aa_wr[i];
+            if (AK == 0 && cx(i) != 0) {
+              put_aa(o, v.x);
+              if (act1) put_aa(o + 1, v.y);
+            } else if (act1) {
+              if (!kCheckBounds || in_range(c0 + o, 2, p.aa_elems, p.state)) Store<S>::st2(cell + o, v);
+            } else {
+              put_aa(o, v.x);
+            }
+          });
+        } else if constexpr (kItemInlineGhosts) {
           // Ghost slots the pair feeds, stored with the cells: at most one for
           // its c_x = +1 values (offset gro from `out`, cell grc) and one for
           // its c_x = -1 values (glo, cell glc); a two-cell last chunk of an
@@ -1428,7 +1504,7 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
             }
           }
         }
-        if (p.io_one && x == p.nx - 1) {
+        if (AK < 0 && p.io_one && x == p.nx - 1) {
           // a one-cell last chunk at an outflow (its cell is the pair's first):
           // the zero-gradient copy beside the cell from the line it just stored
   #pragma unroll
@@ -1462,10 +1538,15 @@ __device__ __forceinline__ void step_tiles(const StepParams& p, long long t0l, i
 // One domain: block b walks its static run of tiles, then shares the rest.
 // VAR: the model-variant form (flags in p); the default form has none of
 // their code.
-template <int XT, int S, bool STATS, bool VAR, int CPT>
+// AK >= 0: one step of the AA-pattern layout (0: step B, 1: step A) with the
+// same tile pipeline, in place (every location is read and written by the
+// same cell: step B reads slot opp(i) at x - c_i and writes slot i at x + c_i,
+// step A reads slot i and writes slot opp(i) of cell x, so no tile's stores
+// touch another tile's sources).
+template <int XT, int S, bool STATS, bool VAR, int CPT, int AK = -1>
 __global__ void __launch_bounds__(block_threads(CPT), 768 / block_threads(CPT)) step_kernel(StepParams p) {
-  step_tiles<XT, S, STATS, VAR, CPT>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
-                                     blockIdx.x, true);
+  step_tiles<XT, S, STATS, VAR, CPT, false, AK>(p, (long long)blockIdx.x * p.static_tiles, p.static_tiles,
+                                                blockIdx.x, true);
 }
 
 // Many independent domains (an ensemble of boxes) in one launch: work item

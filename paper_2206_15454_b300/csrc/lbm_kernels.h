@@ -30,6 +30,13 @@ struct Kern {
   // tau_total with 1/rho^2), selected by the flags in p.
   static void step(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const StepParams& p,
                    bool stats, bool variant, bool pdl);
+  // One step of the AA-pattern layout (p.aa_parity: 0 step B, 1 step A) with
+  // the tile pipeline of the pull scheme (default model): shared memory,
+  // resident blocks per SM and the launch (a programmatic dependent).
+  static void aa_configure(size_t smem);
+  static int aa_occupancy(dim3 block, size_t smem);
+  static void aa_step(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const StepParams& p,
+                      bool stats);
   // One time step of every box of an ensemble (work list w).
   static void batch_step(int nblocks, dim3 block, size_t smem, cudaStream_t s,
                          const StepParams* boxes, const BatchWork* w, bool stats);
@@ -52,10 +59,10 @@ struct Kern {
                           const void* hi);
 };
 
-// AA-pattern storage (lbm_aa.cuh), per storage type (no chunk width).
+// AA-pattern storage (lbm_aa.cuh), per storage type (no chunk width): the
+// boundary fill, and the one-cell step of the model-variant form.
 template <int S>
 struct KernAA {
-  static int cells_per_thread(bool variant);  // of the step kernel
   static int occupancy();  // resident blocks per SM of the step kernel (256 threads)
   static void fill(int blocks, cudaStream_t s, const StepParams& p);
   static void step(int blocks, cudaStream_t s, const AAStep& a, bool stats, bool variant);
