@@ -102,8 +102,9 @@ typedef enum lbm_storage {
      * set (with a ghost layer one cell wide) instead of two, the same bytes per
      * lattice update.  After an even number of steps f*_i(x) sits in slot
      * opp(i) of cell x, after an odd number in slot i of cell x + c_i; steps
-     * alternate between the two and read and write each location from one
-     * thread.  Every boundary kind but LBM_BC_HALO, the model variants and the
+     * alternate between the two, and within a step each location is read and
+     * written for one cell only, so the update is in place.  Every boundary
+     * kind but LBM_BC_HALO, the model variants and the
      * read-outs work as with two sets; not available: the learned correction
      * (lbm_set_correction, lbm_features), ensembles, lbm_test_withhold_fill. */
     LBM_STORAGE_AA = 0x100
