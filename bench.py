@@ -285,7 +285,9 @@ def time_ensemble(P, W, steps, warmup, hbm):
     ms = t0.elapsed_time(t1) / steps
     cells = b.cells
     xt, blocks, tuned_ms = b.tuning()
-    padded = sum(c.ny * c.nz * ((c.nx + xt - 1) // xt) * xt for c in b.cases)
+    def width(nx):  # chunk width 0: each box its own (a single domain's size rule)
+        return xt if xt else (64 if nx <= 64 else 128 if nx <= 128 else 256)
+    padded = sum(c.ny * c.nz * ((c.nx + width(c.nx) - 1) // width(c.nx)) * width(c.nx) for c in b.cases)
     ach = P.BYTES_PER_LUP[P.LBM_F16_SHIFTED] * cells / (ms * 1e-3) / 1e9
     out = {"value": round(cells / ms / 1e3, 1), "unit": "MLUPS", "ms_per_step": ms,
            "steps": steps, "warmup": warmup, "boxes": len(b.cases), "cells": cells,

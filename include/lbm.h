@@ -397,14 +397,17 @@ lbm_status lbm_batch_stats_reset(lbm_batch* b, int32_t enable);
  * of range. */
 lbm_ctx* lbm_batch_box(lbm_batch* b, int32_t i);
 
-/* The launch configuration in use: chunk width (cells), blocks per launch and
- * the measured milliseconds per step of the chosen candidate (0 if untuned). */
+/* The launch configuration in use: chunk width (cells; 0 = every box in the
+ * width a single domain of its x-length takes: 64 up to 64 cells, 128 up to
+ * 128, else 256, one launch per width), blocks per launch and the measured
+ * milliseconds per step of the chosen candidate (0 if untuned; untuned, the
+ * chunk width is the one the longest row takes). */
 lbm_status lbm_batch_tuning(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,
                             double* ms_per_step);
 
 /* The tuner's record: for each candidate it timed (at most cap are written),
- * its chunk width, blocks per launch and milliseconds per step (negative if it
- * failed).  Returns the number of candidates timed (0 when untuned), -1 for
+ * its chunk width (0: each box its own, as above), blocks per launch and
+ * milliseconds per step (negative if it failed).  Returns the number of candidates timed (0 when untuned), -1 for
  * b == NULL. */
 int32_t lbm_batch_candidates(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,
                              double* ms_per_step, int32_t cap);

@@ -94,6 +94,32 @@ def test_features_match_oracle():
     assert np.all(err[6:] < 1e-6)   # leaf-area densities
 
 
+def test_fused_correction_equals_network_on_features():
+    """After a step the correction kernel gathers each 16-column tile's features
+    and runs the network in one pass.  Its field must be the network's forward
+    pass (lbm_mlp_forward: the same tensor-core arithmetic) on lbm_features'
+    output, combined by the correction rule a = (lam dux - dtx, lam duz - dtz),
+    on every column: 70 x 19 = 1330 columns are 83 full warp tiles and a ragged
+    one, over a canopy edge, inflow and outflow."""
+    case = W.canopy_abl(70, 24, 19, h=6.0, canopy_x0=10, xbin=10)
+    th = random_theta(21, scale=0.1)
+    th[M.N_WEIGHTS + 18:M.N_WEIGHTS + 22] = 0.0        # y_mean
+    th[M.N_WEIGHTS + 22:] = 2e-4                       # y_std
+    net = P.CorrectionNet(seed=3)
+    net.set_params(th)
+    d = P.Domain(case)
+    d.step(7)
+    X = d.features()
+    d.set_correction(net, lam=0.05)                    # the field of the current state
+    a = d.correction_field().reshape(-1, 2)
+    Y = net.forward(X)
+    lam = np.float32(0.05)
+    ref = np.stack([lam * Y[:, 0] - Y[:, 2], lam * Y[:, 1] - Y[:, 3]], axis=1)
+    err = np.abs(a - ref).max() / np.abs(ref).max()
+    print(f"fused correction vs network on features: max error / max = {err:.1e}")
+    assert a.shape == ref.shape and err < 1e-6
+
+
 def test_corrected_steps_match_oracle_given_the_same_field():
     th = random_theta(10, scale=0.1)
     th[M.N_WEIGHTS + 18:M.N_WEIGHTS + 22] = 0.0        # y_mean
