@@ -399,7 +399,7 @@ lbm_ctx* lbm_batch_box(lbm_batch* b, int32_t i);
 
 /* The launch configuration in use: chunk width (cells; 0 = every box in the
  * width a single domain of its x-length takes: 64 up to 64 cells, 128 up to
- * 128, else 256, one launch per width), blocks per launch and the measured
+ * 128, else 256, one launch per width and step), blocks per launch and the measured
  * milliseconds per step of the chosen candidate (0 if untuned; untuned, the
  * chunk width is the one the longest row takes). */
 lbm_status lbm_batch_tuning(const lbm_batch* b, int32_t* chunk_width, int32_t* blocks,

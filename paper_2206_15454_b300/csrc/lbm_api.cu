@@ -1253,10 +1253,12 @@ struct lbm_batch {
   int storage = 0, nbins = 1, xt = 0;
   cudaStream_t stream = nullptr;   // the boxes' stream; graphs are launched on it
   cudaStream_t capture = nullptr;  // private stream the graphs are captured on
+  cudaStream_t branch[2] = {nullptr, nullptr};  // the second and third chains' launches
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   char* ws = nullptr;
   bool owns_ws = false;
-  std::vector<BatchWork> work;   // grouped by the boxes' chunk width (64, 128, 256)
-  int group_off[4] = {0, 0, 0, 0};  // work items of group g: [group_off[g], group_off[g + 1])
+  std::vector<BatchWork> work;   // in chains of boxes of one chunk width (64, 128, 256)
+  int group_off[4] = {0, 0, 0, 0};  // work items of chain g: [group_off[g], group_off[g + 1])
   BatchWork* work_dev = nullptr;
   double tuned_ms = 0.0;
   std::vector<double> tried;      // tuner record: (chunk width, blocks, ms per step) per candidate
@@ -1291,6 +1293,15 @@ bool batch_args_ok(int32_t nbox, const lbm_box* boxes, int32_t storage, int32_t 
     if (uses_variant(boxes[i].forcing) || boxes[i].grid.x_lo == LBM_BC_HALO) return false;
   }
   return true;
+}
+
+void free_streams(lbm_batch* b) {
+  if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (int j = 0; j < 2; j++) {
+    if (b->branch[j]) cudaStreamDestroy(b->branch[j]);
+    if (b->join[j]) cudaEventDestroy(b->join[j]);
+  }
 }
 
 void free_graphs(lbm_batch* b) {
@@ -1338,30 +1349,46 @@ lbm_status make_boxes(lbm_batch* b, int32_t nbox, const lbm_box* boxes, double i
 }
 
 // Work items: every box's tiles cut into runs of about `per` tiles, one run
-// per block, grouped by the boxes' chunk width (one launch per group).
+// per block, in chains (one launch per chain and step): the boxes of one
+// chunk width form a chain; when all boxes share one width, alternate boxes
+// form two chains, so that the graph's independent chains overlap each
+// other's launch tails.
 lbm_status make_work(lbm_batch* b, int waves) {
   long long total = 0;
   for (lbm_ctx* c : b->boxes) total += make_params(c).ntiles;
   const lbm_ctx* c0 = b->boxes[0];
   const long long resident = (long long)c0->sm_count * std::max(1, c0->blocks_per_sm);
   const long long per = std::max<long long>(1, (total + waves * resident - 1) / (waves * resident));
-  b->work.clear();
-  for (int g = 0; g < 3; g++) {
-    b->group_off[g] = (int)b->work.size();
-    for (int i = 0; i < (int)b->boxes.size(); i++) {
-      if (b->boxes[i]->sh.xt != kChunkWidths[g]) continue;
-      const long long nt = make_params(b->boxes[i]).ntiles;
-      const long long items = (nt + per - 1) / per;
-      for (long long k = 0; k < items; k++) {
-        BatchWork w;
-        w.box = i;
-        w.t0 = k * nt / items;
-        w.ntile = (int)((k + 1) * nt / items - w.t0);
-        b->work.push_back(w);
+  int widths = 0;
+  for (int g = 0; g < 3; g++)
+    for (const lbm_ctx* c : b->boxes)
+      if (c->sh.xt == kChunkWidths[g]) {
+        widths++;
+        break;
       }
+  const int halves = widths == 1 && b->boxes.size() > 1 ? 2 : 1;
+  b->work.clear();
+  int nch = 0;
+  for (int g = 0; g < 3; g++) {
+    for (int h = 0; h < halves; h++) {
+      b->group_off[nch] = (int)b->work.size();
+      int rank = 0;
+      for (int i = 0; i < (int)b->boxes.size(); i++) {
+        if (b->boxes[i]->sh.xt != kChunkWidths[g] || (rank++ % halves) != h) continue;
+        const long long nt = make_params(b->boxes[i]).ntiles;
+        const long long items = (nt + per - 1) / per;
+        for (long long k = 0; k < items; k++) {
+          BatchWork w;
+          w.box = i;
+          w.t0 = k * nt / items;
+          w.ntile = (int)((k + 1) * nt / items - w.t0);
+          b->work.push_back(w);
+        }
+      }
+      if ((int)b->work.size() > b->group_off[nch]) nch++;
     }
   }
-  b->group_off[3] = (int)b->work.size();
+  for (int g = nch; g < 4; g++) b->group_off[g] = (int)b->work.size();
   if (b->work_dev) cudaFree(b->work_dev);
   b->work_dev = nullptr;
   free_graphs(b);
@@ -1416,7 +1443,7 @@ lbm_status batch_graph(lbm_batch* b, int n, bool stats, cudaGraphExec_t* exec) {
     b->err = "lbm_batch_step: copy of the box parameters failed";
     return LBM_ERR_CUDA;
   }
-  // one box of each chunk-width group: its kernel form, block shape and stages
+  // one box of each chain: its kernel form, block shape and stages
   const lbm_ctx* rep[3] = {nullptr, nullptr, nullptr};
   for (int gi = 0; gi < 3; gi++)
     if (b->group_off[gi + 1] > b->group_off[gi]) rep[gi] = b->boxes[b->work[b->group_off[gi]].box];
@@ -1424,19 +1451,40 @@ lbm_status batch_graph(lbm_batch* b, int n, bool stats, cudaGraphExec_t* exec) {
   cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   cudaError_t e = cudaStreamBeginCapture(b->capture, mode);
   if (e == cudaSuccess) {
-    for (int k = 0; k < n; k++) {
-      const StepParams* P = g.params + (k & 1) * nb;
-      for (int gi = 0; gi < 3; gi++) {
-        const lbm_ctx* cg = rep[gi];
-        if (!cg) continue;
-        const int off = b->group_off[gi], cnt = b->group_off[gi + 1] - off;
+    // The chains hold different boxes, so each is a sequence of n launches
+    // of its own: the first on the capture stream, the others on branches
+    // forked from it and joined at the end, which the graph runs side by side
+    // (one chain's launch tail overlaps another chain's launch).
+    cudaStream_t sg[3] = {nullptr, nullptr, nullptr};
+    int nbr = 0;
+    for (int gi = 0; gi < 3; gi++) {
+      if (!rep[gi]) continue;
+      sg[gi] = nbr == 0 ? b->capture : b->branch[nbr - 1];
+      nbr++;
+    }
+    cudaError_t ef = cudaSuccess;
+    if (nbr > 1) {
+      ef = cudaEventRecord(b->fork, b->capture);
+      for (int j = 0; j + 1 < nbr && ef == cudaSuccess; j++) ef = cudaStreamWaitEvent(b->branch[j], b->fork, 0);
+    }
+    for (int gi = 0; gi < 3 && ef == cudaSuccess; gi++) {
+      const lbm_ctx* cg = rep[gi];
+      if (!cg) continue;
+      const int off = b->group_off[gi], cnt = b->group_off[gi + 1] - off;
+      for (int k = 0; k < n; k++) {
+        const StepParams* P = g.params + (k & 1) * nb;
         dispatch(cg, [&](auto xt, auto s) {
           Kern<decltype(xt)::value, decltype(s)::value>::batch_step(
-              cnt, cg->block, cg->stage_smem, b->capture, P, b->work_dev + off, stats);
+              cnt, cg->block, cg->stage_smem, sg[gi], P, b->work_dev + off, stats);
         });
       }
     }
+    for (int j = 0; j + 1 < nbr && ef == cudaSuccess; j++) {
+      ef = cudaEventRecord(b->join[j], b->branch[j]);
+      if (ef == cudaSuccess) ef = cudaStreamWaitEvent(b->capture, b->join[j], 0);
+    }
     e = cudaStreamEndCapture(b->capture, &graph);
+    if (e == cudaSuccess && ef != cudaSuccess) e = ef;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
@@ -1534,13 +1582,17 @@ lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
   auto bail = [&](lbm_status s) {
     free_boxes(b);
     if (b->owns_ws && b->ws) cudaFree(b->ws);
-    if (b->capture) cudaStreamDestroy(b->capture);
+    free_streams(b);
     delete b;
     return s;
   };
-  if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+  bool made = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) == cudaSuccess;
+  if (made) made = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int j = 0; j < 2 && made; j++)
+    made = cudaStreamCreateWithFlags(&b->branch[j], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) == cudaSuccess;
+  if (!made) {
     cudaGetLastError();
-    b->capture = nullptr;
     return bail(LBM_ERR_CUDA);
   }
   if (workspace) {
@@ -1557,7 +1609,7 @@ lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
   for (int i = 0; i < nbox; i++) max_nx = std::max(max_nx, boxes[i].grid.nx);
   // untuned: the widest chunk that does not exceed the longest row, for every
   // box (each box its own width is a tuner candidate: on the 64-box canopy
-  // ensemble, nx 96..160, it measured 1.006 against 0.979 ms per step)
+  // ensemble, nx 96..160, both measured about 0.93 ms per step)
   int best_xt = chunk_width(max_nx), best_waves = 8;
   double best_ms = 0.0;
   if (tune_steps > 0) {
@@ -1644,7 +1696,7 @@ void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   free_boxes(b);
   if (b->owns_ws && b->ws) cudaFree(b->ws);
-  if (b->capture) cudaStreamDestroy(b->capture);
+  free_streams(b);
   delete b;
 }
 
