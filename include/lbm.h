@@ -375,8 +375,10 @@ size_t lbm_batch_workspace_bytes(int32_t nbox, const lbm_box* boxes, int32_t sto
 /* Create nbox >= 1 boxes, all with the same storage type and statistics bins,
  * initialised as lbm_create does with their own seed and the common
  * init_perturb.  tune_steps > 0 times every candidate launch configuration over
- * that many steps (the boxes are then re-initialised); cuda_stream NULL = legacy
- * default stream.  workspace/workspace_bytes as in lbm_create. */
+ * that many steps (the boxes are then re-initialised); tune_steps = 0 takes the
+ * chunk width of the longest row for every box, tune_steps = -1 each box in its
+ * own (as lbm_create would), both untimed; LBM_ERR_ARG below -1.  cuda_stream
+ * NULL = legacy default stream.  workspace/workspace_bytes as in lbm_create. */
 lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
                             int32_t stats_xbins, double init_perturb, int32_t tune_steps,
                             void* cuda_stream, void* workspace, size_t workspace_bytes,

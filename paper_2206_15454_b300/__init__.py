@@ -603,8 +603,10 @@ def _case_inputs(case):
 
 class Batch:
     """An ensemble of independent boxes (cases with the same storage, statistics
-    bins and perturbation amplitude) advanced by one launch per step, replayed
-    as a CUDA graph.  ``box(i)`` gives a Domain view of box i."""
+    bins and perturbation amplitude) advanced together, all steps replayed as
+    one CUDA graph.  ``tune_steps`` as in lbm_batch_create (> 0: timed
+    candidates; 0: one chunk width for all; -1: each box its own).
+    ``box(i)`` gives a Domain view of box i."""
 
     def __init__(self, cases, storage=LBM_F16_SHIFTED, tune_steps=0, use_torch_workspace=True,
                  stream=None):

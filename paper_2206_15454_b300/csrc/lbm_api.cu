@@ -1568,7 +1568,7 @@ lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
                             lbm_batch** out) {
   if (!out) return LBM_ERR_ARG;
   *out = nullptr;
-  if (!batch_args_ok(nbox, boxes, storage, stats_xbins) || tune_steps < 0 ||
+  if (!batch_args_ok(nbox, boxes, storage, stats_xbins) || tune_steps < -1 ||
       !std::isfinite(init_perturb))
     return LBM_ERR_ARG;
   const size_t need = lbm_batch_workspace_bytes(nbox, boxes, storage, stats_xbins);
@@ -1610,7 +1610,7 @@ lbm_status lbm_batch_create(int32_t nbox, const lbm_box* boxes, int32_t storage,
   // untuned: the widest chunk that does not exceed the longest row, for every
   // box (each box its own width is a tuner candidate: on the 64-box canopy
   // ensemble, nx 96..160, both measured about 0.93 ms per step)
-  int best_xt = chunk_width(max_nx), best_waves = 8;
+  int best_xt = tune_steps < 0 ? 0 : chunk_width(max_nx), best_waves = 8;
   double best_ms = 0.0;
   if (tune_steps > 0) {
     best_ms = 1e300;

@@ -179,7 +179,7 @@ def test_ensemble_arguments_checked_without_a_device():
     assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, 0, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
     arr[1].forcing.u_bulk_target = 0.0
     assert P.lib().lbm_batch_create(0, arr, 1, 1, 0.0, 0, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
-    assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, -1, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
+    assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, -2, None, None, 0, C.byref(b)) == P.LBM_ERR_ARG
     assert P.lib().lbm_batch_create(3, arr, 1, 1, 0.0, 0, None, C.c_void_p(4096), 16,
                                     C.byref(b)) == P.LBM_ERR_OOM
     assert P.lib().lbm_batch_step(None, 1) == P.LBM_ERR_ARG

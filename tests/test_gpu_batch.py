@@ -1,6 +1,6 @@
-"""Ensembles of independent boxes (one launch per step for all boxes, replayed
-as a CUDA graph) against the FP64 oracle and against the same boxes run one
-at a time."""
+"""Ensembles of independent boxes (all boxes' steps in one CUDA graph, a
+launch per chain of boxes and step) against the FP64 oracle and against the
+same boxes run one at a time."""
 import numpy as np
 import pytest
 
@@ -32,11 +32,17 @@ def test_batch_boxes_match_oracle_first_100_steps():
 
 
 @pytest.mark.parametrize("storage", [P.LBM_F32, P.LBM_F16_SHIFTED])
-def test_batch_equals_boxes_run_alone_bitwise(storage):
+@pytest.mark.parametrize("widths", [0, -1])
+def test_batch_equals_boxes_run_alone_bitwise(storage, widths):
     """Same per-cell arithmetic whatever the launch: a box advanced inside the
-    ensemble is bit-identical to the box advanced on its own."""
-    cases = small_boxes()
-    b = P.Batch(cases, storage)
+    ensemble is bit-identical to the box advanced on its own.  x-lengths 49,
+    166, 142, 128, 168: widths 0 puts every box at 256 cells (two chains of
+    alternate boxes), -1 each box in its own width, 64, 128 and 256 (three
+    chains)."""
+    cases = W.ensemble_boxes(n_boxes=5, ny=16, nz=12, nx_range=(40, 200), seed=77)
+    assert sorted(c.nx for c in cases) == [49, 128, 142, 166, 168]
+    b = P.Batch(cases, storage, tune_steps=widths)
+    assert b.tuning()[0] == (256 if widths == 0 else 0)
     b.step(7)
     b.step(7)   # the graph for 7 steps is built once, then replayed from the other parity
     b.step(20)
