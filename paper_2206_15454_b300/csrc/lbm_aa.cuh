@@ -86,45 +86,50 @@ __device__ __forceinline__ int aa_inward(int face, int d) {
 // all in flight at once; a cell on an edge or corner is reached through
 // several faces and writes the same value each time.  The fill reads only
 // slots whose upstream cell is inside, which no fill writes.
+// Grid: blockIdx.z = 5 face + d (30 slices, face and direction uniform per
+// block); the face's two coordinates (a fast, b slow) come from the block
+// and thread indices, a over x (y on the x faces), b over z (y on the z
+// faces), so no index is decoded by division; grid-stride loops cover faces
+// larger than the grid (aa_fill_grid).
 template <int S>
 __global__ void aa_fill_kernel(StepParams p) {
   using T = typename Store<S>::T;
   T* f = static_cast<T*>(p.dst);
-  const long long ax = (long long)p.ny * p.nz, ay = (long long)p.nx * p.nz, az = (long long)p.nx * p.ny;
-  const long long total = 10 * (ax + ay + az);  // 2 faces x 5 directions per axis
+  const int face = (int)blockIdx.z / 5, d = (int)blockIdx.z - 5 * face;
+  const int na = face < 2 ? p.ny : p.nx, nb = face < 4 ? p.nz : p.ny;
+  const int i = aa_inward(face, d);
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous step has completed
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-       k += (long long)gridDim.x * blockDim.x) {
-    long long r = k;
-    int face, x, y, z;
-    if (r < 10 * ax) {
-      face = (int)(r / (5 * ax));
-      r -= face * 5 * ax;
-      y = (int)(r % p.ny);
-      z = (int)((r / p.ny) % p.nz);
-      x = face ? p.nx - 1 : 0;
-    } else if ((r -= 10 * ax) < 10 * ay) {
-      face = 2 + (int)(r / (5 * ay));
-      r -= (face - 2) * 5 * ay;
-      x = (int)(r % p.nx);
-      z = (int)((r / p.nx) % p.nz);
-      y = face == 3 ? p.ny - 1 : 0;
-    } else {
-      r -= 10 * ay;
-      face = 4 + (int)(r / (5 * az));
-      r -= (face - 4) * 5 * az;
-      x = (int)(r % p.nx);
-      y = (int)((r / p.nx) % p.ny);
-      z = face == 5 ? p.nz - 1 : 0;
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
+      int x, y, z;
+      if (face < 2) {
+        x = face ? p.nx - 1 : 0;
+        y = a;
+        z = b;
+      } else if (face < 4) {
+        x = a;
+        y = face == 3 ? p.ny - 1 : 0;
+        z = b;
+      } else {
+        x = a;
+        y = b;
+        z = face == 5 ? p.nz - 1 : 0;
+      }
+      const float v = aa_pull<S>(p, i, x, y, z);
+      const long long at = p.aa_parity == 0 ? aa_index(p, opp(i), x - cx(i), y - cy(i), z - cz(i))
+                                            : aa_index(p, i, x, y, z);
+      if (!kCheckBounds || in_range(at, 1, p.aa_elems, p.state)) Store<S>::st(f + at, v);
     }
-    const long long area = face < 2 ? ax : face < 4 ? ay : az;
-    const int i = aa_inward(face, (int)(r / area));
-    const float v = aa_pull<S>(p, i, x, y, z);
-    const long long at = p.aa_parity == 0 ? aa_index(p, opp(i), x - cx(i), y - cy(i), z - cz(i))
-                                          : aa_index(p, i, x, y, z);
-    if (!kCheckBounds || in_range(at, 1, p.aa_elems, p.state)) Store<S>::st(f + at, v);
   }
+}
+
+// Launch shape of aa_fill_kernel: 256 threads along the fast coordinate
+// (x, or y on the x faces), one block row per slow coordinate up to the
+// grid's y limit, 30 face-direction slices.
+inline dim3 aa_fill_grid(int nx, int ny, int nz) {
+  const int na = nx > ny ? nx : ny, nb = nz > ny ? nz : ny;
+  return dim3((unsigned)((na + 255) / 256), (unsigned)(nb < 65535 ? nb : 65535), 30u);
 }
 
 // Per-launch element offsets of the 19 reads and the 19 writes relative to

@@ -695,9 +695,6 @@ namespace {
 lbm_status aa_step(lbm_ctx* c) {
   const StepParams p = make_params(c);
   const lbm_grid& g = c->grid;
-  // one fill thread per (face cell, entering direction)
-  const long long fill = 10ll * ((long long)g.ny * g.nz + (long long)g.nx * g.nz + (long long)g.nx * g.ny);
-  const int fblocks = (int)std::max<long long>(1, std::min<long long>((fill + 255) / 256, c->sm_count * 16ll));
   AAStep a;
   a.p = p;
   const long long ys = c->ash.pitch, zs = (g.ny + 2) * ys, qs = (g.nz + 2) * zs;
@@ -721,7 +718,7 @@ lbm_status aa_step(lbm_ctx* c) {
     // the boundary fill, then the step on the tile pipeline (both
     // programmatic dependents of the kernel before them)
     dispatch(c, [&](auto xt, auto s) {
-      KernAA<decltype(s)::value>::fill(fblocks, c->stream, p);
+      KernAA<decltype(s)::value>::fill(c->stream, p);
       Kern<decltype(xt)::value, decltype(s)::value>::aa_step(dim3(step_grid(c)), c->block, c->stage_smem,
                                                              c->stream, p, c->stats_on);
     });
@@ -732,7 +729,7 @@ lbm_status aa_step(lbm_ctx* c) {
     return LBM_OK;
   }
   dispatch_s(c, [&](auto s) {
-    KernAA<decltype(s)::value>::fill(fblocks, c->stream, p);
+    KernAA<decltype(s)::value>::fill(c->stream, p);
     KernAA<decltype(s)::value>::step(grid, c->stream, a, c->stats_on, uses_variant(c->forcing));
   });
   CK(c, cudaGetLastError());

@@ -64,7 +64,7 @@ struct Kern {
 template <int S>
 struct KernAA {
   static int occupancy();  // resident blocks per SM of the step kernel (256 threads)
-  static void fill(int blocks, cudaStream_t s, const StepParams& p);
+  static void fill(cudaStream_t s, const StepParams& p);  // grid: aa_fill_grid
   static void step(int blocks, cudaStream_t s, const AAStep& a, bool stats, bool variant);
   static void init(int blocks, cudaStream_t s, const StepParams& p, const InitParams& ip);
   static void mass(int blocks, cudaStream_t s, const StepParams& p, double* partial);
