@@ -23,6 +23,9 @@ CASES = W.small_cases() + [
     W.canopy_abl(257, 9, 5, h=3.0, canopy_x0=60, xbin=64).replace(name="outflow_257"),
     W.small_cases()[2].replace(name="canopy_variants", drag_streamwise_only=1, forcing_scheme=1,
                                sgs_rho_power=2),
+    # faces of 70,000 rows, more than the boundary fill's grid has block rows
+    # (65,535): the fill's grid-stride loop over a face's slow coordinate
+    W.poiseuille(2, 3, 70000).replace(name="tall_z", init_perturb=0.03, seed=11),
 ]
 
 

@@ -80,6 +80,17 @@ for c in cases:
         assert err <= (1e-6 if st == P.LBM_F32 | P.LBM_STORAGE_AA else 5e-3), (c.name, "AA", st, err)
         d.close()
         o.close()
+# ... and on faces longer than the fill grid's 65,535 block rows (its
+# grid-stride loop)
+c = W.poiseuille(2, 3, 70000).replace(name="tall_z", init_perturb=0.03, seed=11)
+d, o = P.Domain(c, P.LBM_F32 | P.LBM_STORAGE_AA), oracle.Oracle(c)
+d.step(11)
+o.step(11)
+a, b = d.get_f(), o.get_f()
+err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+assert err <= 1e-6, (c.name, "AA", err)
+d.close()
+o.close()
 from paper_2206_15454_b300 import slabs as S
 c = W.channel_les(150, 9, 6).replace(u_bulk_target=0.0, ctrl_gain=0.0)
 whole = P.Domain(c)
