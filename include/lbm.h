@@ -197,9 +197,12 @@ lbm_status lbm_stats(lbm_ctx* ctx, double* out, size_t n, int64_t* samples);
 
 /* Pipelined read-out of the same averages, for a caller that reads every
  * step's result without idling the GPU: lbm_stats_begin enqueues, on the
- * context's stream after the work already enqueued, one asynchronous copy of
- * the accumulators and health flags into a pinned slot of the library (two
- * slots; LBM_ERR_ARG when both hold a pending read-out) and returns at once;
+ * context's stream after the work already enqueued, one copy of the
+ * accumulators and health flags into a pinned slot of the library (a small
+ * kernel writing the slot through its mapped device address, launched as a
+ * programmatic dependent so that the steps around it keep their overlap; two
+ * slots; LBM_ERR_ARG when both hold a pending read-out; LBM_ERR_CUDA when the
+ * pinned slot has no device address) and returns at once;
  * lbm_stats_end waits for the oldest pending read-out and fills `out` and
  * `samples` exactly as lbm_stats would have at the point of the matching
  * begin (LBM_ERR_ARG when none is pending).  A step enqueued between the two

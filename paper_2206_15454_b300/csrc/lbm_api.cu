@@ -158,6 +158,7 @@ struct lbm_ctx {
   float* feat_buf = nullptr;     // staging buffer of lbm_features
   unsigned char* readout = nullptr;  // pinned host copies of the statistics and health flags:
                                      // slot 0 for lbm_stats, slots 1 and 2 for the pipelined read-out
+  unsigned char* readout_dev = nullptr;  // the same buffer's device address (mapped pinned memory)
   cudaEvent_t rd_ev[2] = {nullptr, nullptr};  // completion of the pipelined copies
   int64_t rd_samples[2] = {0, 0};             // steps accumulated when each copy was enqueued
   int rd_first = 0, rd_pending = 0;           // oldest pending slot (0/1), pending count
@@ -803,6 +804,13 @@ lbm_status ensure_readout(lbm_ctx* c, const char* who) {
     c->readout = nullptr;
     return fail(c, LBM_ERR_OOM, std::string(who) + ": cudaMallocHost of the readout buffer failed");
   }
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->readout_dev), c->readout, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(c->readout);
+    c->readout = nullptr;
+    c->readout_dev = nullptr;
+    return fail(c, LBM_ERR_CUDA, std::string(who) + ": the readout buffer has no device address");
+  }
   return LBM_OK;
 }
 
@@ -866,8 +874,24 @@ lbm_status lbm_stats_begin(lbm_ctx* c) {
   if (s != LBM_OK) return s;
   const int k = (c->rd_first + c->rd_pending) & 1;
   if (!c->rd_ev[k]) CK(c, cudaEventCreateWithFlags(&c->rd_ev[k], cudaEventDisableTiming));
-  CK(c, cudaMemcpyAsync(readout_slot(c, 1 + k), c->ws + c->L.stats_off, readout_bytes(c),
-                        cudaMemcpyDeviceToHost, c->stream));
+  {
+    // the read-out kernel (a programmatic dependent of the step before it)
+    // writes the slot through the pinned buffer's device address
+    static_assert(sizeof(DevState) % 16 == 0 && kAlign % 16 == 0, "the read-out moves 16-byte words");
+    const long long n16 = (long long)(readout_bytes(c) / 16);
+    const size_t slot = (size_t)(readout_slot(c, 1 + k) - c->readout);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)std::max<long long>(1, std::min<long long>((n16 + 255) / 256, 148)));
+    cfg.blockDim = dim3(256);
+    cfg.stream = c->stream;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(c, cudaLaunchKernelEx(&cfg, readout_kernel, reinterpret_cast<const uint4*>(c->ws + c->L.stats_off),
+                             reinterpret_cast<uint4*>(c->readout_dev + slot), n16));
+  }
   CK(c, cudaEventRecord(c->rd_ev[k], c->stream));
   c->rd_samples[k] = c->stats_samples;
   c->rd_pending++;

@@ -67,4 +67,19 @@ __global__ void mass_final_kernel(const double* partial, int n, double base, dou
   }
 }
 
+// The pipelined statistics read-out (lbm_stats_begin): n16 16-byte words of
+// the plane sums and health flags (adjacent in the workspace) into a slot of
+// the context's pinned host buffer, through its mapped device address.  It
+// runs as a programmatic dependent of the step before it and lets the next
+// step's launch proceed from its start, so consecutive steps keep their
+// programmatic overlap (an asynchronous copy between two steps broke it).
+__global__ void readout_kernel(const uint4* __restrict__ src, uint4* dst, long long n16) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the step before has completed
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n16;
+       k += (long long)gridDim.x * blockDim.x)
+    dst[k] = src[k];
+  __threadfence_system();
+}
+
 }  // namespace lbm
