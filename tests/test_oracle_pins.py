@@ -212,7 +212,8 @@ def test_smagorinsky_channel_matches_semi_analytic():
 
 def test_poiseuille_startup_series():
     """32^3 channel from rest, 2000 steps: transient series solution of the
-    diffusion equation with the steady slip added (BASELINE laminar case)."""
+    diffusion equation with the steady slip added (the laminar Poiseuille
+    channel: 32 cells across, g = 1e-6, tau = 0.8)."""
     H, g, tau, t = 32, 1e-6, 0.8, 2000
     nu, lam = (tau - 0.5) / 3, (tau - 0.5) ** 2
     o = oracle.Oracle(W.poiseuille(1, H, 1, g=g, tau=tau))
